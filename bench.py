@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark: DOF-steps/s of the implicit ADS/IGA Newmark step on one GB300.
+
+Workload (one bench "step"): the 128^3-element scalar P-wave configuration,
+p = 2 and p = 3 (one simulation each, 130^3 and 131^3 DOFs), tau = 2e-3,
+200 Newmark steps per simulation, zero initial state, Ricker (f = 8,
+t0 = 1/8) x Gaussian (sigma = 0.02) source at a seeded interior point, FP32
+path (FP32 state and sweeps, FP64 1D factors).  DOF counts include boundary
+coefficients.  The L2 cache is flushed (a 512 MB write) before every timed
+step; inputs stay resident in HBM.
+
+  value  : device time (CUDA events on the simulations' stream), whole job
+  e2e    : the same metric through the C ABI with pinned host buffers: per
+           step set_state(u, v, a) from host, 200 steps, get_state to host
+  fp64   : the FP64 path on the same workload (the path the FP32 one beats)
+  roofline: dominant kernel, algorithmic bytes / its CUDA-event time
+  cpu_baseline: the FP64 CPU oracle on a bounded sample of the workload
+
+--impl reference runs the CPU oracle as the reference arm (there is no
+reference implementation of this paper; the oracle is the plain restatement).
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF-steps/s (implicit ADS/IGA Newmark step, FP32 path)"
+UNIT = "DOF-steps/s"
+NE, NSTEPS, PS = 128, 200, (2, 3)
+WORKLOAD = "pwave_ricker_128cubed_p2p3_200steps"
+
+# algorithmic bytes per interior DOF of one launch (FP32), see the design doc
+ALG_BYTES = {
+    "rhs_xy_sweep": 8,      # read p, write x-and-y-swept field
+    "rhs_x_sweep": 8,       # read p, write x-swept field
+    "y_sweep": 8,           # read, write
+    "z_sweep_update": 24,   # read swept field, p, q; write p, q, a (a is written in profiled steps)
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 4 + i and r[4 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_sims(precision, torch, ads, wl, stream=None):
+    sims = []
+    for p in PS:
+        case = wl.ricker_case(ne=NE, p=p)
+        sim = ads.Simulation(case.n_elem, case.p, case.tau, precision=precision, stream=stream)
+        sim.set_source(case.source)
+        sim.set_gaussian_state(None, None)
+        sims.append(sim)
+    return sims
+
+
+def dofs(sim):
+    return int(np.prod(sim.n))
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1911_08158_gb300 as ads
+    from paper_1911_08158_gb300 import workloads as wl
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()   # all simulations and the timing events share it
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sims = make_sims("fp32", torch, ads, wl, stream)
+    dof_steps = sum(dofs(s) for s in sims) * NSTEPS
+
+    def bench_step():
+        for s in sims:
+            s.step(NSTEPS)
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time per step, L2 flushed in between)
+    times = []
+    l0 = ads.launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bench_step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        barrier()
+        wall = time.perf_counter() - wall0
+    launches = ads.launch_count() - l0
+    t_dev = float(sum(times))
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = dof_steps * args.steps * ws / t_dev
+
+    # ---- per-kernel times (CUDA events between the kernels of single steps)
+    kt = {}
+    for s in sims:
+        for _ in range(5):
+            for name, ms in s.profile_step():
+                kt.setdefault((name, s.p), []).append(ms)
+    torch.cuda.synchronize()
+    tot = {}
+    for (name, p), v in kt.items():
+        tot[name] = tot.get(name, 0.0) + float(np.mean(v))
+    dom = max(tot, key=tot.get)
+    # per launch of the dominant kernel: average over the two simulations
+    per_launch = []
+    for s in sims:
+        m = [float(np.mean(v)) for (n, p), v in kt.items() if n == dom and p == s.p]
+        if m:
+            mx, my, mz = s.n[0] - 2, s.n[1] - 2, s.n[2] - 2
+            per_launch.append((ALG_BYTES[dom] * mx * my * mz, m[0] / 1e3))
+    alg_bytes = float(np.mean([b for b, _ in per_launch]))
+    dur = float(np.mean([t for _, t in per_launch]))
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / dur / 1e9
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+        ent = prof.get(dom)
+        if ent and ent.get("workload") == WORKLOAD:
+            traffic = ent.get("bytes_per_launch")
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": "measured" if peaks else "fallback",
+                "kernel_share": {k: round(v / sum(tot.values()), 4) for k, v in tot.items()},
+                "kernel_ms": {k: round(v, 5) for k, v in tot.items()}}
+
+    # ---- accuracy of the FP32 path against the FP64 path (fresh runs)
+    acc = {}
+    s64 = make_sims("fp64", torch, ads, wl, stream)
+    s32 = make_sims("fp32", torch, ads, wl, stream)
+    for a, b in zip(s64, s32):
+        a.step(NSTEPS)
+        b.step(NSTEPS)
+        ua = a.get_state(fields=("u",))[0]
+        ub = b.get_state(fields=("u",))[0]
+        acc["p%d" % a.p] = float(np.linalg.norm(ub - ua) / np.linalg.norm(ua))
+
+    # ---- FP64 path throughput (same workload, fewer steps)
+    for s in s64:
+        s.step(16)
+    torch.cuda.synchronize()
+    k64 = max(1, min(args.steps, 3))
+    t64 = 0.0
+    for _ in range(k64):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in s64:
+            s.step(NSTEPS)
+        e1.record(stream)
+        e1.synchronize()
+        t64 += e0.elapsed_time(e1) / 1e3
+    fp64 = {"value": dof_steps * k64 / t64, "ms_per_step": t64 / k64 * 1e3, "steps": k64}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    host = []
+    for s in sims:
+        bufs = [torch.zeros(s.shape, dtype=torch.float64).pin_memory() for _ in range(3)]
+        u, v, a = s.get_state()
+        for b, x in zip(bufs, (u, v, a)):
+            b.copy_(torch.from_numpy(x))
+        host.append(bufs)
+    h2d = sum(3 * 8 * dofs(s) for s in sims)
+    d2h = h2d
+    lib = ads.library()
+    ke = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        for s, bufs in zip(sims, host):
+            ptr = [b.data_ptr() for b in bufs]
+            ads.ads._check(lib.ads_set_state(s.handle, ptr[0], ptr[1], ptr[2], s.count, ads.ADS_HOST))
+            s.step(NSTEPS)
+            ads.ads._check(lib.ads_get_state(s.handle, ptr[0], ptr[1], ptr[2], s.count, ads.ADS_HOST))
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    e2e = {"value": dof_steps * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "steps": ke}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_elem": NE, "p": list(PS), "tau": 2e-3, "newmark_steps": NSTEPS,
+                   "dofs": [dofs(s) for s in sims], "dof_steps_per_step": dof_steps,
+                   "l2": "flushed (512 MB write) before each timed step", "parallelism": "replicas" if ws > 1 else "single"},
+        "e2e": e2e, "gpu_launches": int(launches), "wall_s": wall,
+        "fp64": fp64, "rel_l2_fp32_vs_fp64_u": acc,
+        "roofline": roofline, "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def oracle_sample(seconds: float, p: int = 2):
+    """Time the FP64 CPU oracle on the benchmark workload (128^3, p) for at
+    least `seconds` of stepping; setup (1D matrices, 3D source quadrature) is
+    not timed.  Returns (DOF-steps/s, steps, elapsed, threads)."""
+    import oracle as ora
+    from paper_1911_08158_gb300 import workloads as wl
+
+    case = wl.ricker_case(ne=NE, p=p)
+    s = ora.Space(case.n_elem, case.p)
+    G = s.load_gauss(case.source["amp"], case.source["center"], case.source["den"])
+    z = s.zeros()
+    a = s.pwave_accel(z, 0.0, 1.0, G)
+    u, v = z, z
+    n, t = 0, 0.0
+    while t < seconds:
+        t0 = time.perf_counter()
+        u, v, a = s.pwave_run(u, v, a, case.tau, 1, step0=n, G=G)
+        t += time.perf_counter() - t0
+        n += 1
+    return int(np.prod(s.n)) * n / t, n, t, ora.num_threads()
+
+
+def cpu_baseline(seconds: float):
+    val, n, t, th = oracle_sample(seconds)
+    return {"value": val, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": "%d Newmark steps of the 128^3 p=2 workload (FP64 oracle, OpenMP over lines), %.1f s" % (n, t)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per_step = max(1.0, args.cpu_seconds / max(args.steps, 1))
+    for _ in range(args.warmup):
+        oracle_sample(0.0)
+    vals, tt, nn = [], 0.0, 0
+    for _ in range(args.steps):
+        v, n, t, th = oracle_sample(per_step)
+        vals.append(v)
+        tt += t
+        nn += n
+    value = float(np.prod([NE + 2] * 3)) * nn / tt
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "n_elem": NE, "p": [2], "sample": "Newmark steps of the p=2 simulation"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                            "sample": "%d Newmark steps of the 128^3 p=2 workload in %.1f s" % (nn, tt)},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def profile_case(ne, p: int, steps: int):
+    """Small fixed case for ncu captures: one FP32 simulation with ne
+    (n or nx,ny,nz) elements (no timing), a few steps via the profiling entry."""
+    import torch
+
+    import paper_1911_08158_gb300 as ads
+    from paper_1911_08158_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    case = wl.ricker_case(ne=ne, p=p)
+    sim = ads.Simulation(case.n_elem, case.p, case.tau, precision="fp32")
+    sim.set_source(case.source)
+    sim.set_gaussian_state(None, None)
+    sim.step(2)                      # graph path, as in the benchmark
+    for _ in range(steps):
+        sim.profile_step()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": ne, "p": p, "steps": steps, "device_bytes": sim.device_bytes}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", default="", help="run a small case (n or nx,ny,nz elements) for ncu and exit")
+    ap.add_argument("--profile-p", type=int, default=2)
+    args = ap.parse_args()
+    if args.profile_case:
+        ne = tuple(int(v) for v in args.profile_case.split(","))
+        profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

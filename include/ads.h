@@ -1,0 +1,208 @@
+/*
+ * ads.h -- C ABI of the GB300 alternating-direction isogeometric wave solver.
+ *
+ * The method (Los, Behnoudfar, Paszynski, Calo, "Fast isogeometric solvers
+ * for hyperbolic wave propagation problems"):
+ *   - space: tensor-product B-splines of degree p on [0,L0]x[0,L1]x[0,L2],
+ *     open uniform knots, n_a = n_elem[a] + p functions per axis (Sec. 2);
+ *     homogeneous Dirichlet boundary (the first and last function per axis
+ *     are fixed at zero);
+ *   - scalar wave u_tt - c2 Lap u = f (Sec. 2): implicit Newmark step with
+ *     the Kronecker split operator (eq. pwave2)
+ *         (Mx+eta Kx)(x)(My+eta Ky)(x)(Mz+eta Kz) a_{n+1}
+ *             = F_{n+1} - K (u_n + tau v_n + eta a_n),   eta = c2 tau^2/4,
+ *         u_{n+1} = u_n + tau v_n + eta (a_n + a_{n+1}),
+ *         v_{n+1} = v_n + tau/2 (a_n + a_{n+1}),
+ *     K = c2 (Kx.My.Mz + Mx.Ky.Mz + Mx.My.Kz); the split inverse is three
+ *     directional banded solves (Appendix);
+ *   - linear elasticity rho u_tt = div sigma + f (Sec. 5): three-level
+ *     alternating-triangular scheme (eqs. decom, pre, corr, spill, gen),
+ *         D (U^{n+1} - 2U^n + U^{n-1}) / tau^2 + Ups U^n = f^n,
+ *         D = (rho M + tau^2/2 Ups1~)(rho M)^{-1}(rho M + tau^2/2 Ups2~).
+ *
+ * Conventions for every call:
+ *   - Return ADS_OK (0) or a negative ADS_ERR_* code; ads_last_error() gives
+ *     a message (thread-local, valid until the next call on that thread).
+ *   - Field arrays cross the boundary as FP64 coefficient arrays of the FULL
+ *     space, [comp][z][y][x] with x fastest, count = comps*n0*n1*n2 doubles;
+ *     boundary coefficients are ignored on input and zero on output.
+ *   - mem = ADS_HOST: plain host pointers (pageable or pinned); the caller
+ *     owns them, the library copies and keeps no reference.
+ *     mem = ADS_DEVICE: device pointers on the simulation's device.
+ *   - Device memory of a simulation is owned by the library; it comes from
+ *     the allocator in ads_options_t (e.g. a framework's caching allocator)
+ *     or from cudaMalloc.
+ *   - Work is ordered on the simulation's CUDA stream; ads_step returns
+ *     without waiting, ads_get_state / ads_energy / ads_sync wait.
+ *   - A simulation is not thread-safe: one caller thread at a time.
+ */
+#ifndef ADS_H
+#define ADS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADS_OK 0
+#define ADS_ERR_INVALID_ARG (-1)
+#define ADS_ERR_OOM (-2)
+#define ADS_ERR_CUDA (-3)
+#define ADS_ERR_TIMEOUT (-4)
+#define ADS_ERR_UNSUPPORTED (-5)
+
+enum { ADS_SCALAR_WAVE = 0, ADS_ELASTIC = 1 };   /* ads_material_t.kind */
+enum { ADS_FP64 = 0, ADS_FP32 = 1 };             /* ads_options_t.precision */
+enum { ADS_HOST = 0, ADS_DEVICE = 1 };           /* memory kind of a pointer */
+
+/* ads_apply operators (all FP64, on one scalar field of the full space) */
+enum {
+    ADS_OP_MASS = 0,        /* out = (Mx.My.Mz) in                          */
+    ADS_OP_STIFF = 1,       /* out = K in, K = c2 (Kx.My.Mz + Mx.Ky.Mz + Mx.My.Kz) */
+    ADS_OP_MASS_SOLVE = 2,  /* out = (Mx.My.Mz)^{-1} in, exact (Appendix)    */
+    ADS_OP_SPLIT_SOLVE = 3  /* out = ((Mx+eta Kx).(My+eta Ky).(Mz+eta Kz))^{-1} in */
+};
+
+typedef struct ads_sim ads_sim_t;     /* opaque, library-owned */
+
+typedef struct {
+    int n_elem[3];        /* elements along x, y, z (>= 1) */
+    double length[3];     /* domain extents (> 0) */
+} ads_grid_t;
+
+typedef struct {
+    int kind;             /* ADS_SCALAR_WAVE or ADS_ELASTIC */
+    double c2;            /* scalar wave speed squared (u_tt - c2 Lap u = f) */
+    double lambda, mu;    /* Lame parameters (elasticity) */
+    double rho;           /* density (elasticity) */
+} ads_material_t;
+
+typedef void *(*ads_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*ads_free_fn)(void *ptr, void *ctx);
+
+typedef struct {
+    int precision;        /* ADS_FP64, or ADS_FP32: FP32 state and sweeps,
+                             1D factors computed in FP64 and rounded */
+    int device;           /* CUDA device ordinal; -1 = the current device */
+    void *stream;         /* cudaStream_t for all work (not the legacy
+                             default stream: steps are replayed as CUDA
+                             graphs); NULL = a stream the library creates */
+    ads_alloc_fn alloc;   /* device allocator; NULL = cudaMalloc */
+    ads_free_fn free;     /* matching free; required when alloc is set */
+    void *alloc_ctx;      /* passed to alloc/free */
+    int tile_lines;       /* y rows per CTA of the RHS + x-sweep kernel (a
+                             tile of one z-plane); 0 = library choice */
+} ads_options_t;
+
+/* Gaussian g(x) = amp * exp(-|x - center|^2 / den); for elasticity the
+ * vector field is dir * g (dir ignored for the scalar wave). */
+typedef struct {
+    double amp;
+    double dir[3];
+    double center[3];
+    double den;
+} ads_gaussian_t;
+
+/* Source f(x, t) = r(t) g(x): Ricker wavelet
+ * r(t) = (1 - 2 pi^2 f^2 (t-t0)^2) exp(-pi^2 f^2 (t-t0)^2) times a Gaussian. */
+typedef struct {
+    ads_gaussian_t shape;
+    double freq;
+    double t0;
+} ads_source_t;
+
+/* Create a simulation (setup of Sec. 2 / Appendix): builds the 1D knot
+ * vectors, Gauss rules and banded 1D matrices in FP64, factors the 1D
+ * directional operators (banded LU without pivoting; all are SPD), uploads
+ * them and allocates the state on the device.  p in 1..4; tau > 0;
+ * opts may be NULL (FP64, current device, library stream, cudaMalloc).
+ * State starts at zero with step counter 0.  Errors: INVALID_ARG (sizes,
+ * tau, material), UNSUPPORTED (p, or a grid beyond the kernels' limits:
+ * n_elem + p - 2 <= 512 per axis), OOM, CUDA. */
+int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *mat,
+               const ads_options_t *opts, ads_sim_t **out);
+
+/* Free all device memory of the simulation (waits for its stream). */
+void ads_destroy(ads_sim_t *sim);
+
+/* Full basis counts per axis (n[3]) and field components (1 or 3). */
+int ads_dims(const ads_sim_t *sim, int *n, int *comps);
+
+/* Source term f(x,t) = r(t) g(x) (Sec. 2: F_{n+1} = (f(t_{n+1}), w)); its
+ * load vector is integrated with the (p+1)-point Gauss rule.  NULL removes
+ * the source.  Scalar wave: F_{n+1} enters step n -> n+1; elasticity: f^n
+ * at level n (eq. gen). */
+int ads_set_source(ads_sim_t *sim, const ads_source_t *src);
+
+/* Set the state from L2 projections (Appendix: isogeometric L2 projection,
+ * exact Kronecker mass solve) of Gaussian initial displacement u0 and
+ * velocity v0 (either may be NULL = zero); resets the step counter to 0.
+ * Scalar wave: a0 = M^{-1}(F(0) - K u0).  Elasticity: U^{-1} = U0 - tau V0
+ * + tau^2/2 A0, A0 = (rho M)^{-1}(f^0 - Ups U0). */
+int ads_set_gaussian_state(ads_sim_t *sim, const ads_gaussian_t *u0, const ads_gaussian_t *v0);
+
+/* Set the state from coefficient arrays (count = comps*n0*n1*n2 each).
+ * Scalar wave: u, v required; a may be NULL (then a = M^{-1}(F(t_n) - K u)).
+ * Elasticity: u = U^n, v = V^n; a must be NULL; U^{n-1} as in
+ * ads_set_gaussian_state.  The step counter is left unchanged. */
+int ads_set_state(ads_sim_t *sim, const double *u, const double *v, const double *a, size_t count,
+                  int mem);
+
+/* Read the state; any output may be NULL.  Scalar wave: u_n, v_n, a_n.
+ * Elasticity: u = U^n, v = (U^n - U^{n-1})/tau; a must be NULL.
+ * Waits for the stream. */
+int ads_get_state(ads_sim_t *sim, double *u, double *v, double *a, size_t count, int mem);
+
+/* Advance nsteps >= 0 time steps (asynchronous on the stream). */
+int ads_step(ads_sim_t *sim, int nsteps);
+
+/* Advance several simulations (same device) by nsteps each in one launch
+ * sequence; simulations of equal shape and precision share launches. */
+int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps);
+
+/* Wait for the simulation's stream; reports asynchronous CUDA errors. */
+int ads_sync(ads_sim_t *sim);
+
+/* Step counter n (time t_n = n tau). */
+int ads_get_step(const ads_sim_t *sim, long long *n);
+
+/* Energies at step n.  Scalar wave: kinetic 1/2 v^T M v, potential
+ * 1/2 u^T K u; modified kinetic 1/2 v^T (G~ - eta K) v (with potential, the
+ * exactly conserved invariant when f = 0).  Elasticity: kinetic
+ * 1/2 rho V^T M V with V = (U^n - U^{n-1})/tau, potential 1/2 U^T Ups U,
+ * kin_mod = the conserved invariant of the three-level scheme at n-1/2
+ * (Sec. 6).  Reductions in FP64 with compensated summation.  Any output
+ * may be NULL.  Waits for the stream. */
+int ads_energy(ads_sim_t *sim, double *kinetic, double *potential, double *kin_mod);
+
+/* Apply one of the ADS_OP_* operators of this simulation's space to a
+ * scalar field (count = n0*n1*n2 doubles), in FP64 on the device.  Waits. */
+int ads_apply(ads_sim_t *sim, int op, const double *in, double *out, size_t count, int mem);
+
+/* Checkpoint: the raw device state (all precisions bit-exact) plus the
+ * step counter.  bytes = ads_checkpoint_bytes(); save waits for the stream. */
+size_t ads_checkpoint_bytes(const ads_sim_t *sim);
+int ads_checkpoint_save(ads_sim_t *sim, void *host_buf, size_t bytes);
+int ads_checkpoint_load(ads_sim_t *sim, const void *host_buf, size_t bytes);
+
+/* Device bytes held by the simulation (state, scratch, factors). */
+size_t ads_device_bytes(const ads_sim_t *sim);
+
+/* Measurement: run ONE time step with CUDA events recorded on the
+ * simulation's stream between its kernels; fills names[i] (static strings)
+ * and ms[i] (device time of kernel i) for i < min(cap, *count).  Advances the
+ * state like ads_step(sim, 1).  Waits. */
+int ads_profile_step(ads_sim_t *sim, const char **names, float *ms, int cap, int *count);
+
+/* Kernel launches issued by this library since load (all simulations). */
+long long ads_launch_count(void);
+
+const char *ads_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADS_H */

@@ -1,0 +1,1039 @@
+// api.cpp -- the C ABI of include/ads.h: simulation objects, device tables,
+// the per-step launch sequence (captured into CUDA graphs), boundary
+// conversions, operators, energies and checkpoints.
+#include "ads.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "setup1d.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define ADS_CK(expr)                                                                              \
+    do {                                                                                          \
+        cudaError_t e_ = (expr);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ADS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+}  // namespace
+
+// Device tables of one directional factor set (banded LU factors plus the
+// segment tables of the partitioned solve) in one contiguous buffer laid out
+// as the kernels' shared-memory image (see LineDev), precision T.
+struct LineTables {
+    void *base = nullptr;
+    int S = 0;
+    int bytes = 0;
+};
+
+enum { SET_SPLIT = 0, SET_MASS = 1, SET_IDENT = 2, SET_ELAS0 = 3, SET_ELAS1 = 4, NSETS = 5 };
+
+// Device copy of a set of FP64 host tables in precision T.
+struct TableSet {
+    void *M[3] = {}, *K[3] = {}, *B[3] = {};   // operator bands [m_pad][2p+1]
+    LineTables line[NSETS][3];                 // per factor set and axis
+    void *img[NSETS] = {};                     // K1 images (x and y tables of a set)
+    int img_bytes[NSETS] = {};
+    void *gband[3] = {};                       // bands of M + eta c2 K (energies)
+    void *src[3] = {};                         // separable source load vectors
+};
+
+struct ads_sim {
+    int kind = ADS_SCALAR_WAVE, prec = ADS_FP64, p = 2, device = 0;
+    ads::Axis1D ax[3];
+    double tau = 0, c2 = 1, lam = 1, mu = 1, rho = 1;
+    ads::Dims d{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    ads_alloc_fn alloc = nullptr;
+    ads_free_fn dfree = nullptr;
+    void *actx = nullptr;
+    std::map<void *, size_t> live;
+    size_t bytes = 0;
+    TableSet t64, t32;
+    // host FP64 copies used to assemble the kernels' table images
+    std::vector<double> hM[3], hK[3], hsrc[3];
+    std::vector<double> hline[NSETS][3];
+    int lineS[3] = {0, 0, 0};
+    // scalar-wave state (precision prec): p = u + tau v + eta a, q = tau v + tau^2/2 a
+    void *P = nullptr, *Q = nullptr, *A = nullptr, *X = nullptr;
+    long long *d_step = nullptr;
+    long long h_step = 0;
+    int *d_err = nullptr;   // device error word written by bounded waits
+    bool has_src = false;
+    ads_source_t src{};
+    // kernel tiling of K1 per precision
+    int ty[2] = {0, 0}, tz[2] = {0, 0}, fuse[2] = {0, 0};
+    int seg = 32;           // register segment width of the line solves
+    // graphs: chunk size -> executable graph
+    std::map<int, cudaGraphExec_t> graphs;
+    bool warmed = false;
+};
+
+namespace {
+
+size_t elem(const ads_sim *s) { return s->prec == ADS_FP64 ? 8 : 4; }
+
+void *dalloc(ads_sim *s, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (s->alloc) {
+        p = s->alloc(bytes, s->actx);
+    } else {
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    if (p) {
+        s->live[p] = bytes;
+        s->bytes += bytes;
+    }
+    return p;
+}
+
+void dfree(ads_sim *s, void *p)
+{
+    if (!p) return;
+    auto it = s->live.find(p);
+    if (it != s->live.end()) {
+        s->bytes -= it->second;
+        s->live.erase(it);
+    }
+    if (s->dfree) s->dfree(p, s->actx);
+    else cudaFree(p);
+}
+
+// RAII scratch for one API call
+struct Scratch {
+    ads_sim *s;
+    std::vector<void *> ptrs;
+    explicit Scratch(ads_sim *s_) : s(s_) {}
+    void *get(size_t bytes)
+    {
+        void *p = dalloc(s, bytes);
+        if (p) ptrs.push_back(p);
+        return p;
+    }
+    ~Scratch()
+    {
+        if (!ptrs.empty()) cudaStreamSynchronize(s->stream);
+        for (void *p : ptrs) dfree(s, p);
+    }
+};
+
+template <typename T>
+int upload(ads_sim *s, const std::vector<double> &h, void **dst)
+{
+    std::vector<T> tmp(h.begin(), h.end());
+    void *p = dalloc(s, tmp.size() * sizeof(T));
+    if (!p) return fail(ADS_ERR_OOM, "device allocation failed (tables)");
+    ADS_CK(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = p;
+    return ADS_OK;
+}
+
+ads::Factor identity_factor(int m, int p)
+{
+    ads::Factor f;
+    f.m = m;
+    f.p = p;
+    f.v.assign((size_t)m * (2 * p + 1), 0.0);
+    for (int i = 0; i < m; ++i) f.v[(size_t)i * (2 * p + 1) + p] = 1.0;
+    return f;
+}
+
+// Rows padded to a whole number of segments: m_pad = S * seg.
+int padded(const ads_sim *s, int m) { return (m + s->seg - 1) / s->seg * s->seg; }
+
+// band rows [m][2p+1] -> [m_pad][2p+1], zero rows appended
+std::vector<double> pad_rows(const std::vector<double> &v, int m, int width, int m_pad, bool identity_factor)
+{
+    std::vector<double> out((size_t)m_pad * width, 0.0);
+    std::copy(v.begin(), v.begin() + (size_t)m * width, out.begin());
+    if (identity_factor)
+        for (int i = m; i < m_pad; ++i) out[(size_t)i * width + width / 2] = 1.0;   // 1/u_0 = 1
+    return out;
+}
+
+// host image of one factor set: fac | phi | psi | Phi | Psi (padded rows)
+std::vector<double> line_image(const ads_sim *s, const ads::Factor &f, int *S)
+{
+    ads::Partition P = ads::partition_fixed(f, s->seg);
+    const int mp = padded(s, f.m), W = 2 * f.p + 1;
+    std::vector<double> img = pad_rows(f.v, f.m, W, mp, true);
+    auto add = [&](const std::vector<double> &v) { img.insert(img.end(), v.begin(), v.end()); };
+    add(pad_rows(P.phi, f.m, f.p, mp, false));
+    add(pad_rows(P.psi, f.m, f.p, mp, false));
+    add(P.Phi);
+    add(P.Psi);
+    *S = P.S;
+    return img;
+}
+
+template <typename T>
+int upload_padded(ads_sim *s, const std::vector<double> &h, void **dst, int *bytes)
+{
+    std::vector<T> tmp(h.begin(), h.end());
+    while ((tmp.size() * sizeof(T)) % 16) tmp.push_back(T(0));
+    void *p = dalloc(s, tmp.size() * sizeof(T));
+    if (!p) return fail(ADS_ERR_OOM, "device allocation failed (tables)");
+    ADS_CK(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = p;
+    if (bytes) *bytes = (int)(tmp.size() * sizeof(T));
+    return ADS_OK;
+}
+
+// K1 image of factor set `set`: bMx bKx | bMy bKy | fx | fy | x tables | y tables
+template <typename T>
+int upload_rhs_image(ads_sim *s, TableSet &ts, int set)
+{
+    if (s->hline[set][0].empty()) return ADS_OK;
+    std::vector<double> img;
+    auto add = [&](const std::vector<double> &v) { img.insert(img.end(), v.begin(), v.end()); };
+    add(s->hM[0]);
+    add(s->hK[0]);
+    add(s->hM[1]);
+    add(s->hK[1]);
+    for (int a = 0; a < 2; ++a) {
+        const size_t mp = (size_t)padded(s, s->ax[a].m);
+        if (s->hsrc[a].size() == mp) add(s->hsrc[a]);
+        else img.insert(img.end(), mp, 0.0);
+    }
+    add(s->hline[set][0]);
+    add(s->hline[set][1]);
+    if (ts.img[set]) {
+        dfree(s, ts.img[set]);
+        ts.img[set] = nullptr;
+    }
+    return upload_padded<T>(s, img, &ts.img[set], &ts.img_bytes[set]);
+}
+
+template <typename T>
+int upload_line(ads_sim *s, int set, int axis, LineTables *lt)
+{
+    int rc = upload_padded<T>(s, s->hline[set][axis], &lt->base, &lt->bytes);
+    lt->S = s->lineS[axis];
+    return rc;
+}
+
+template <typename T>
+int build_tables(ads_sim *s, TableSet &ts)
+{
+    const double eta = 0.25 * s->tau * s->tau;
+    // host images (FP64), once
+    if (s->hM[0].empty()) {
+        for (int a = 0; a < 3; ++a) {
+            const ads::Axis1D &ax = s->ax[a];
+            const int mp = padded(s, ax.m), W = 2 * ax.p + 1;
+            s->hM[a] = pad_rows(ax.M.v, ax.m, W, mp, false);
+            s->hK[a] = pad_rows(ax.K.v, ax.m, W, mp, false);
+            int S = 0;
+            try {
+                s->hline[SET_IDENT][a] = line_image(s, identity_factor(ax.m, ax.p), &S);
+                s->hline[SET_MASS][a] = line_image(s, ads::factor_axis(ax, 0.0), &S);
+                if (s->kind == ADS_SCALAR_WAVE) {
+                    s->hline[SET_SPLIT][a] = line_image(s, ads::factor_axis(ax, eta * s->c2), &S);
+                } else {
+                    const double c[2] = {2 * s->mu + s->lam, s->mu};
+                    for (int k = 0; k < 2; ++k)
+                        s->hline[SET_ELAS0 + k][a] =
+                            line_image(s, ads::factor_axis(ax, s->tau * s->tau * c[k] / (4 * s->rho)), &S);
+                }
+            } catch (const std::exception &e) {
+                return fail(ADS_ERR_INVALID_ARG, e.what());
+            }
+            s->lineS[a] = S;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        const ads::Axis1D &ax = s->ax[a];
+        const int mp = padded(s, ax.m), W = 2 * ax.p + 1;
+        int rc;
+        if ((rc = upload<T>(s, s->hM[a], &ts.M[a]))) return rc;
+        if ((rc = upload<T>(s, s->hK[a], &ts.K[a]))) return rc;
+        if ((rc = upload<T>(s, pad_rows(ax.B.v, ax.m, W, mp, false), &ts.B[a]))) return rc;
+        for (int set = 0; set < NSETS; ++set)
+            if (!s->hline[set][a].empty() && (rc = upload_line<T>(s, set, a, &ts.line[set][a]))) return rc;
+        if (s->kind == ADS_SCALAR_WAVE) {
+            std::vector<double> g(ax.M.v.size());
+            for (size_t i = 0; i < g.size(); ++i) g[i] = ax.M.v[i] + eta * s->c2 * ax.K.v[i];
+            if ((rc = upload<T>(s, g, &ts.gband[a]))) return rc;
+        }
+    }
+    for (int set = 0; set < NSETS; ++set) {
+        int rc = upload_rhs_image<T>(s, ts, set);
+        if (rc) return rc;
+    }
+    return ADS_OK;
+}
+
+template <typename T>
+ads::LineDev<T> line_dev(const LineTables &lt)
+{
+    ads::LineDev<T> l;
+    l.base = (const T *)lt.base;
+    l.S = lt.S;
+    l.bytes = lt.bytes;
+    return l;
+}
+
+int segs(const ads_sim *s, int m) { return (m + s->seg - 1) / s->seg; }
+
+void choose_tiles(ads_sim *s)
+{
+    const int Sx = segs(s, s->d.mx), Sy = segs(s, s->d.my);
+    for (int pi = 0; pi < 2; ++pi) {
+        const int el = pi == 0 ? 8 : 4;
+        const int my = s->d.my;
+        const size_t budget_fused = 220 * 1024, budget = 110 * 1024;
+        const char *env = std::getenv("ADS_RHS_TILE");   // rows per tile, for experiments
+        int ty = 0;
+        auto fits = [&](int t, size_t b) { return ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy) <= b; };
+        if (env && std::sscanf(env, "%d", &ty) == 1 && ty > 0) {
+            ty = std::min(ty, my);
+            if (!fits(ty, budget_fused)) ty = 0;
+        }
+        if (ty == 0) {
+            if (fits(my, budget_fused)) {
+                ty = my;
+            } else {
+                ty = std::min(my, 32);
+                while (ty > 1 && !fits(ty, budget)) ty /= 2;
+            }
+        }
+        s->ty[pi] = ty;
+        s->tz[pi] = 1;
+        s->fuse[pi] = (ty == my) ? 1 : 0;
+    }
+}
+
+template <typename T>
+const TableSet &tables_for(const ads_sim *s)
+{
+    return sizeof(T) == 8 ? s->t64 : s->t32;
+}
+
+template <typename T>
+ads::RhsArgs<T> rhs_args(const ads_sim *s, const T *in, T *out, int set, int toff, bool with_src)
+{
+    const TableSet &ts = tables_for<T>(s);
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    ads::RhsArgs<T> a{};
+    a.in = in;
+    a.out = out;
+    a.d = s->d;
+    for (int k = 0; k < 3; ++k) {
+        a.bandM[k].v = (const T *)ts.M[k];
+        a.bandK[k].v = (const T *)ts.K[k];
+        a.bandM[k].lo = a.bandK[k].lo = s->ax[k].lo;
+        a.bandM[k].hi = a.bandK[k].hi = s->ax[k].hi;
+    }
+    a.lx = line_dev<T>(ts.line[set][0]);
+    a.ly = line_dev<T>(ts.line[set][1]);
+    a.img = (const T *)ts.img[set];
+    a.img_bytes = ts.img_bytes[set];
+    a.c2 = (T)s->c2;
+    if (with_src && s->has_src) {
+        a.src.fx = (const T *)ts.src[0];
+        a.src.fy = (const T *)ts.src[1];
+        a.src.fz = (const T *)ts.src[2];
+        a.src.amp = 1.0;   // amplitude folded into the load vectors
+        a.src.freq = s->src.freq;
+        a.src.t0 = s->src.t0;
+    }
+    a.step = s->d_step;
+    a.toff = toff;
+    a.tau = s->tau;
+    a.ty = s->ty[pi];
+    a.err = s->d_err;
+    return a;
+}
+
+// out = A^{-1} R along y then z (mode 0) after K1 has done x (and maybe y)
+template <typename T>
+int sweeps_yz(ads_sim *s, T *data, int set, bool y_done)
+{
+    ads::ColArgs<T> c{};
+    c.d = s->d;
+    c.mode = 0;
+    c.in = data;
+    c.out = data;
+    c.err = s->d_err;
+    if (!y_done) {
+        c.axis = 1;
+        c.ln = line_dev<T>(tables_for<T>(s).line[set][1]);
+        ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    }
+    c.axis = 2;
+    c.ln = line_dev<T>(tables_for<T>(s).line[set][2]);
+    ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    return ADS_OK;
+}
+
+// Generic Kronecker solve of an arbitrary FP64 interior field (in place).
+int kron_solve64(ads_sim *s, double *data, int set)
+{
+    // the factor rows open the line buffer
+    ADS_CK(ads::launch_solve_x<double>(s->p, (const double *)s->t64.line[set][0].base, data, s->d, s->stream));
+    return sweeps_yz<double>(s, data, set, false);
+}
+
+// out = c2 K in (FP64), through the fused RHS kernel with identity factors:
+// K1 computes fac_x^{-1}(F - c2 K in) = -c2 K in.
+int apply_stiff64(ads_sim *s, const double *in, double *out)
+{
+    ads::RhsArgs<double> a = rhs_args<double>(s, in, out, SET_IDENT, 0, false);
+    ADS_CK(ads::launch_rhs<double>(s->p, s->seg, a, s->stream));
+    ADS_CK(ads::launch_axpby(0.0, out, -1.0, out, s->d.count(), s->stream));
+    return ADS_OK;
+}
+
+// out = (A_x.A_y.A_z) in with bands (FP64), scratch tmp
+int apply_kron64(ads_sim *s, void *const *band, const double *in, double *out, double *tmp)
+{
+    ADS_CK(ads::launch_axis_apply<double>(s->p, (const double *)band[0], 0, in, out, s->d, 1.0, 0.0, 0, s->stream));
+    ADS_CK(ads::launch_axis_apply<double>(s->p, (const double *)band[1], 1, out, tmp, s->d, 1.0, 0.0, 0, s->stream));
+    ADS_CK(ads::launch_axis_apply<double>(s->p, (const double *)band[2], 2, tmp, out, s->d, 1.0, 0.0, 0, s->stream));
+    return ADS_OK;
+}
+
+int dot64(ads_sim *s, const double *x, const double *y, double *result_host)
+{
+    Scratch sc(s);
+    const int nb = 304;
+    double *part = (double *)sc.get(sizeof(double) * 2 * nb + sizeof(double));
+    if (!part) return fail(ADS_ERR_OOM, "scratch allocation failed");
+    double *res = part + 2 * nb;
+    ADS_CK(ads::launch_dot(x, y, s->d.count(), part, nb, res, s->stream));
+    ADS_CK(cudaMemcpyAsync(result_host, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    return ADS_OK;
+}
+
+// stage a full FP64 field (host or device) into an interior FP64 array
+int stage_in(ads_sim *s, Scratch &sc, const double *src, int mem, size_t count, double *dst_interior, double scale)
+{
+    const double *full = src;
+    if (mem == ADS_HOST) {
+        double *tmp = (double *)sc.get(count * sizeof(double));
+        if (!tmp) return fail(ADS_ERR_OOM, "scratch allocation failed");
+        ADS_CK(cudaMemcpyAsync(tmp, src, count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        full = tmp;
+    }
+    ADS_CK(ads::launch_pack<double>(full, dst_interior, s->d, scale, s->stream));
+    return ADS_OK;
+}
+
+int stage_out(ads_sim *s, Scratch &sc, const double *interior, double *dst, int mem, size_t count)
+{
+    double *full = dst;
+    if (mem == ADS_HOST) {
+        full = (double *)sc.get(count * sizeof(double));
+        if (!full) return fail(ADS_ERR_OOM, "scratch allocation failed");
+    }
+    ADS_CK(ads::launch_unpack<double>(interior, full, s->d, s->stream));
+    if (mem == ADS_HOST) {
+        ADS_CK(cudaMemcpyAsync(dst, full, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    }
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    return ADS_OK;
+}
+
+// A bounded wait that gave up records a nonzero word; report it once.
+int check_device_error(ads_sim *s)
+{
+    int e = 0;
+    ADS_CK(cudaMemcpy(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        cudaMemset(s->d_err, 0, sizeof(int));
+        if (e == 2) return fail(ADS_ERR_CUDA, "a kernel found a misaligned TMA shared-memory address and skipped it");
+        return fail(ADS_ERR_TIMEOUT, "a device-side wait timed out (TMA transfer did not complete)");
+    }
+    return ADS_OK;
+}
+
+size_t full_count(const ads_sim *s)
+{
+    return (size_t)(s->d.mx + 2) * (s->d.my + 2) * (s->d.mz + 2) * (s->kind == ADS_ELASTIC ? 3 : 1);
+}
+
+// a = M^{-1}(F(t_n) - K u) for an FP64 interior u
+int consistent_accel64(ads_sim *s, const double *u, double *a)
+{
+    ads::RhsArgs<double> r = rhs_args<double>(s, u, a, SET_MASS, 0, true);
+    ADS_CK(ads::launch_rhs<double>(s->p, s->seg, r, s->stream));
+    return sweeps_yz<double>(s, a, SET_MASS, r.ty == s->d.my);
+}
+
+template <typename T>
+int set_pq(ads_sim *s, const double *u, const double *v, const double *a)
+{
+    ADS_CK(ads::launch_uva_to_pq<T>(u, v, a, (T *)s->P, (T *)s->Q, (T *)s->A, s->d, s->tau, s->stream));
+    return ADS_OK;
+}
+
+template <typename T>
+int get_uva(ads_sim *s, double *u, double *v, double *a)
+{
+    ADS_CK(ads::launch_pq_to_uva<T>((const T *)s->P, (const T *)s->Q, (const T *)s->A, u, v, a, s->d, s->tau,
+                                    s->stream));
+    return ADS_OK;
+}
+
+// Optional per-kernel event recording (measurement entry point only).
+struct KernelTimer {
+    std::vector<cudaEvent_t> ev;
+    std::vector<const char *> names;
+    int mark(cudaStream_t st, const char *name)
+    {
+        cudaEvent_t e;
+        ADS_CK(cudaEventCreate(&e));
+        ADS_CK(cudaEventRecord(e, st));
+        ev.push_back(e);
+        names.push_back(name);
+        return ADS_OK;
+    }
+    ~KernelTimer()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+// One scalar-wave step: K1 (RHS + x [+ y]), K2 (y) if needed, K3 (z + update).
+template <typename T>
+int pwave_step(ads_sim *s, bool write_a, KernelTimer *kt = nullptr)
+{
+    const TableSet &ts = tables_for<T>(s);
+    ads::RhsArgs<T> r = rhs_args<T>(s, (const T *)s->P, (T *)s->X, SET_SPLIT, 1, true);
+    const bool fused = r.ty == s->d.my;
+    int rc;
+    if (kt && (rc = kt->mark(s->stream, fused ? "rhs_xy_sweep" : "rhs_x_sweep"))) return rc;
+    ADS_CK(ads::launch_rhs<T>(s->p, s->seg, r, s->stream));
+    ads::ColArgs<T> c{};
+    c.d = s->d;
+    c.in = (const T *)s->X;
+    c.out = (T *)s->X;
+    c.err = s->d_err;
+    if (!fused) {
+        c.axis = 1;
+        c.mode = 0;
+        c.ln = line_dev<T>(ts.line[SET_SPLIT][1]);
+        if (kt && (rc = kt->mark(s->stream, "y_sweep"))) return rc;
+        ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    }
+    c.axis = 2;
+    c.mode = 1;
+    c.ln = line_dev<T>(ts.line[SET_SPLIT][2]);
+    c.P = (T *)s->P;
+    c.Q = (T *)s->Q;
+    c.A = (T *)s->A;
+    c.tau2 = (T)(s->tau * s->tau);
+    c.write_a = write_a ? 1 : 0;
+    c.step = s->d_step;
+    if (kt && (rc = kt->mark(s->stream, "z_sweep_update"))) return rc;
+    ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    if (kt && (rc = kt->mark(s->stream, ""))) return rc;
+    return ADS_OK;
+}
+
+int step_once(ads_sim *s, bool write_a)
+{
+    return s->prec == ADS_FP64 ? pwave_step<double>(s, write_a) : pwave_step<float>(s, write_a);
+}
+
+int get_graph(ads_sim *s, int chunk, cudaGraphExec_t *out)
+{
+    auto it = s->graphs.find(chunk);
+    if (it != s->graphs.end()) {
+        *out = it->second;
+        return ADS_OK;
+    }
+    cudaGraph_t g = nullptr;
+    const unsigned long long before = ads::g_launches;
+    ADS_CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = ADS_OK;
+    for (int i = 0; i < chunk && rc == ADS_OK; ++i) rc = step_once(s, i == chunk - 1);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    ads::g_launches = before;
+    if (rc != ADS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ADS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ADS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    s->graphs[chunk] = ge;
+    *out = ge;
+    return ADS_OK;
+}
+
+// K1 images carry the source vectors: rebuild after a source change, and
+// drop captured graphs (they hold the old image pointers)
+int rebuild_images(ads_sim *s)
+{
+    for (int set = 0; set < NSETS; ++set) {
+        int rc = upload_rhs_image<double>(s, s->t64, set);
+        if (rc) return rc;
+        if (s->prec == ADS_FP32 && (rc = upload_rhs_image<float>(s, s->t32, set))) return rc;
+    }
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    return ADS_OK;
+}
+
+int launches_per_step(const ads_sim *s)
+{
+    const int pi = s->prec == ADS_FP64 ? 0 : 1;
+    return s->fuse[pi] ? 2 : 3;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char *ads_last_error(void) { return g_err.c_str(); }
+
+long long ads_launch_count(void) { return (long long)ads::g_launches; }
+
+int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *mat, const ads_options_t *opts,
+               ads_sim_t **out)
+{
+    if (!grid || !mat || !out) return fail(ADS_ERR_INVALID_ARG, "ads_create: null argument");
+    *out = nullptr;
+    if (p < 1 || p > 4) return fail(ADS_ERR_UNSUPPORTED, "ads_create: p must be in 1..4");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(ADS_ERR_INVALID_ARG, "ads_create: tau must be > 0");
+    if (mat->kind != ADS_SCALAR_WAVE && mat->kind != ADS_ELASTIC)
+        return fail(ADS_ERR_INVALID_ARG, "ads_create: unknown material kind");
+    if (mat->kind == ADS_ELASTIC) return fail(ADS_ERR_UNSUPPORTED, "ads_create: elasticity not built in this library");
+    if (mat->kind == ADS_SCALAR_WAVE && !(mat->c2 > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_create: c2 must be > 0");
+    for (int a = 0; a < 3; ++a) {
+        if (grid->n_elem[a] < 1) return fail(ADS_ERR_INVALID_ARG, "ads_create: n_elem must be >= 1");
+        if (!(grid->length[a] > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_create: length must be > 0");
+        if (grid->n_elem[a] + p - 2 < 1) return fail(ADS_ERR_INVALID_ARG, "ads_create: no interior basis function");
+        if (grid->n_elem[a] + p - 2 > 512) return fail(ADS_ERR_UNSUPPORTED, "ads_create: more than 512 unknowns per axis");
+    }
+    ads_options_t o{};
+    o.precision = ADS_FP64;
+    o.device = -1;
+    if (opts) o = *opts;
+    if (o.precision != ADS_FP64 && o.precision != ADS_FP32) return fail(ADS_ERR_INVALID_ARG, "ads_create: precision");
+    if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(ADS_ERR_INVALID_ARG, "ads_create: alloc and free go together");
+
+    ads_sim *s = new (std::nothrow) ads_sim();
+    if (!s) return fail(ADS_ERR_OOM, "ads_create: host allocation failed");
+    s->kind = mat->kind;
+    s->prec = o.precision;
+    s->p = p;
+    s->tau = tau;
+    s->c2 = mat->c2;
+    s->lam = mat->lambda;
+    s->mu = mat->mu;
+    s->rho = mat->rho;
+    s->alloc = o.alloc;
+    s->dfree = o.free;
+    s->actx = o.alloc_ctx;
+    int dev = o.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            delete s;
+            return fail(ADS_ERR_CUDA, "ads_create: no CUDA device");
+        }
+    }
+    s->device = dev;
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        delete s;
+        return fail(ADS_ERR_CUDA, "ads_create: cudaSetDevice failed");
+    }
+    if (o.stream) {
+        s->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return fail(ADS_ERR_CUDA, "ads_create: stream creation failed");
+        }
+        s->own_stream = true;
+    }
+    try {
+        for (int a = 0; a < 3; ++a) s->ax[a] = ads::build_axis(grid->n_elem[a], p, grid->length[a]);
+    } catch (const std::exception &e) {
+        ads_destroy(s);
+        return fail(ADS_ERR_INVALID_ARG, e.what());
+    }
+    s->d.mx = s->ax[0].m;
+    s->d.my = s->ax[1].m;
+    s->d.mz = s->ax[2].m;
+    s->d.sx = (s->d.mx + 7) / 8 * 8;
+    s->seg = 32;
+    choose_tiles(s);
+    if (o.tile_lines > 0) {
+        // user override of the tile height (rows of one z-plane per CTA)
+        const int pi = s->prec == ADS_FP64 ? 0 : 1;
+        s->ty[pi] = std::min(s->d.my, o.tile_lines);
+        s->fuse[pi] = s->ty[pi] == s->d.my;
+    }
+    int rc = build_tables<double>(s, s->t64);
+    if (rc == ADS_OK && s->prec == ADS_FP32) rc = build_tables<float>(s, s->t32);
+    if (rc != ADS_OK) {
+        std::string msg = g_err;
+        ads_destroy(s);
+        return fail(rc, msg);
+    }
+    const size_t n = (size_t)s->d.count() * elem(s);
+    s->P = dalloc(s, n);
+    s->Q = dalloc(s, n);
+    s->A = dalloc(s, n);
+    s->X = dalloc(s, n);
+    s->d_step = (long long *)dalloc(s, sizeof(long long));
+    s->d_err = (int *)dalloc(s, sizeof(int));
+    if (!s->P || !s->Q || !s->A || !s->X || !s->d_step || !s->d_err) {
+        ads_destroy(s);
+        return fail(ADS_ERR_OOM, "ads_create: device allocation of the state failed");
+    }
+    cudaMemsetAsync(s->P, 0, n, s->stream);
+    cudaMemsetAsync(s->Q, 0, n, s->stream);
+    cudaMemsetAsync(s->A, 0, n, s->stream);
+    cudaMemsetAsync(s->X, 0, n, s->stream);
+    cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->stream);
+    cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        ads_destroy(s);
+        return fail(ADS_ERR_CUDA, "ads_create: initialisation failed");
+    }
+    *out = s;
+    return ADS_OK;
+}
+
+void ads_destroy(ads_sim_t *s)
+{
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    std::vector<void *> ptrs;
+    for (auto &kv : s->live) ptrs.push_back(kv.first);
+    for (void *p : ptrs) dfree(s, p);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+int ads_dims(const ads_sim_t *s, int *n, int *comps)
+{
+    if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_dims: null sim");
+    if (n) {
+        n[0] = s->d.mx + 2;
+        n[1] = s->d.my + 2;
+        n[2] = s->d.mz + 2;
+    }
+    if (comps) *comps = s->kind == ADS_ELASTIC ? 3 : 1;
+    return ADS_OK;
+}
+
+int ads_set_source(ads_sim_t *s, const ads_source_t *src)
+{
+    if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_set_source: null sim");
+    cudaSetDevice(s->device);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(ADS_ERR_CUDA, "ads_set_source: stream error");
+    for (TableSet *ts : {&s->t64, &s->t32})
+        for (int a = 0; a < 3; ++a) {
+            dfree(s, ts->src[a]);
+            ts->src[a] = nullptr;
+        }
+    s->has_src = false;
+    for (int a = 0; a < 3; ++a) s->hsrc[a].clear();
+    if (!src) return rebuild_images(s);
+    if (!(src->shape.den > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_set_source: den must be > 0");
+    s->src = *src;
+    for (int a = 0; a < 3; ++a) {
+        std::vector<double> g = ads::gaussian_load(s->ax[a], src->shape.center[a], src->shape.den);
+        if (a == 0)
+            for (double &v : g) v *= src->shape.amp;
+        g.resize(padded(s, s->ax[a].m), 0.0);   // padded like every 1D table
+        s->hsrc[a] = g;
+        int rc = upload<double>(s, g, &s->t64.src[a]);
+        if (rc) return rc;
+        if (s->prec == ADS_FP32 && (rc = upload<float>(s, g, &s->t32.src[a]))) return rc;
+    }
+    s->has_src = true;
+    return rebuild_images(s);
+}
+
+int ads_set_state(ads_sim_t *s, const double *u, const double *v, const double *a, size_t count, int mem)
+{
+    if (!s || !u || !v) return fail(ADS_ERR_INVALID_ARG, "ads_set_state: null argument");
+    if (count != full_count(s)) return fail(ADS_ERR_INVALID_ARG, "ads_set_state: count does not match the space");
+    if (mem != ADS_HOST && mem != ADS_DEVICE) return fail(ADS_ERR_INVALID_ARG, "ads_set_state: mem");
+    cudaSetDevice(s->device);
+    Scratch sc(s);
+    const size_t ni = (size_t)s->d.count() * sizeof(double);
+    double *tu = (double *)sc.get(ni), *tv = (double *)sc.get(ni), *ta = (double *)sc.get(ni);
+    if (!tu || !tv || !ta) return fail(ADS_ERR_OOM, "ads_set_state: scratch allocation failed");
+    int rc;
+    if ((rc = stage_in(s, sc, u, mem, count, tu, 1.0))) return rc;
+    if ((rc = stage_in(s, sc, v, mem, count, tv, 1.0))) return rc;
+    if (a) {
+        if ((rc = stage_in(s, sc, a, mem, count, ta, 1.0))) return rc;
+    } else {
+        ADS_CK(cudaMemcpyAsync(s->d_step, &s->h_step, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+        if ((rc = consistent_accel64(s, tu, ta))) return rc;
+    }
+    rc = s->prec == ADS_FP64 ? set_pq<double>(s, tu, tv, ta) : set_pq<float>(s, tu, tv, ta);
+    if (rc) return rc;
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    return ADS_OK;
+}
+
+int ads_set_gaussian_state(ads_sim_t *s, const ads_gaussian_t *u0, const ads_gaussian_t *v0)
+{
+    if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_set_gaussian_state: null sim");
+    cudaSetDevice(s->device);
+    Scratch sc(s);
+    const size_t ni = (size_t)s->d.count() * sizeof(double);
+    double *tu = (double *)sc.get(ni), *tv = (double *)sc.get(ni), *ta = (double *)sc.get(ni);
+    if (!tu || !tv || !ta) return fail(ADS_ERR_OOM, "ads_set_gaussian_state: scratch allocation failed");
+    const ads_gaussian_t *gs[2] = {u0, v0};
+    double *dst[2] = {tu, tv};
+    for (int f = 0; f < 2; ++f) {
+        if (!gs[f]) {
+            ADS_CK(cudaMemsetAsync(dst[f], 0, ni, s->stream));
+            continue;
+        }
+        if (!(gs[f]->den > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_set_gaussian_state: den must be > 0");
+        // separable: projection = (Mx^-1 gx) (x) (My^-1 gy) (x) (Mz^-1 gz), done
+        // on the device as the outer product of the loads and a mass solve
+        void *g[3];
+        for (int a = 0; a < 3; ++a) {
+            std::vector<double> h = ads::gaussian_load(s->ax[a], gs[f]->center[a], gs[f]->den);
+            g[a] = sc.get(h.size() * sizeof(double));
+            if (!g[a]) return fail(ADS_ERR_OOM, "scratch allocation failed");
+            ADS_CK(cudaMemcpyAsync(g[a], h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+            ADS_CK(cudaStreamSynchronize(s->stream));
+        }
+        ADS_CK(ads::launch_outer((const double *)g[0], (const double *)g[1], (const double *)g[2], gs[f]->amp,
+                                 dst[f], s->d, s->stream));
+        int rc = kron_solve64(s, dst[f], SET_MASS);
+        if (rc) return rc;
+    }
+    s->h_step = 0;
+    ADS_CK(cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->stream));
+    int rc = consistent_accel64(s, tu, ta);
+    if (rc) return rc;
+    rc = s->prec == ADS_FP64 ? set_pq<double>(s, tu, tv, ta) : set_pq<float>(s, tu, tv, ta);
+    if (rc) return rc;
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    return ADS_OK;
+}
+
+int ads_get_state(ads_sim_t *s, double *u, double *v, double *a, size_t count, int mem)
+{
+    if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_get_state: null sim");
+    if (count != full_count(s)) return fail(ADS_ERR_INVALID_ARG, "ads_get_state: count does not match the space");
+    if (mem != ADS_HOST && mem != ADS_DEVICE) return fail(ADS_ERR_INVALID_ARG, "ads_get_state: mem");
+    cudaSetDevice(s->device);
+    Scratch sc(s);
+    const size_t ni = (size_t)s->d.count() * sizeof(double);
+    double *tu = (double *)sc.get(ni), *tv = (double *)sc.get(ni), *ta = (double *)sc.get(ni);
+    if (!tu || !tv || !ta) return fail(ADS_ERR_OOM, "ads_get_state: scratch allocation failed");
+    int rc = s->prec == ADS_FP64 ? get_uva<double>(s, tu, tv, ta) : get_uva<float>(s, tu, tv, ta);
+    if (rc) return rc;
+    double *outs[3] = {u, v, a};
+    double *ins[3] = {tu, tv, ta};
+    for (int f = 0; f < 3; ++f)
+        if (outs[f] && (rc = stage_out(s, sc, ins[f], outs[f], mem, count))) return rc;
+    return check_device_error(s);
+}
+
+int ads_step(ads_sim_t *s, int nsteps)
+{
+    if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_step: null sim");
+    if (nsteps < 0) return fail(ADS_ERR_INVALID_ARG, "ads_step: nsteps < 0");
+    if (nsteps == 0) return ADS_OK;
+    cudaSetDevice(s->device);
+    int rc;
+    if (!s->warmed) {
+        // first launch outside capture (sets kernel attributes)
+        if ((rc = step_once(s, nsteps == 1))) return rc;
+        s->warmed = true;
+        s->h_step += 1;
+        --nsteps;
+        if (nsteps == 0) return ADS_OK;
+    }
+    const int chunk = 16;
+    if (nsteps >= chunk) {
+        cudaGraphExec_t ge;
+        if ((rc = get_graph(s, chunk, &ge))) return rc;
+        const int full = nsteps / chunk;
+        for (int i = 0; i < full; ++i) ADS_CK(cudaGraphLaunch(ge, s->stream));
+        ads::g_launches += (unsigned long long)full * chunk * launches_per_step(s);
+        nsteps -= full * chunk;
+        s->h_step += (long long)full * chunk;
+    }
+    if (nsteps > 0) {
+        cudaGraphExec_t ge;
+        if ((rc = get_graph(s, nsteps, &ge))) return rc;
+        ADS_CK(cudaGraphLaunch(ge, s->stream));
+        ads::g_launches += (unsigned long long)nsteps * launches_per_step(s);
+        s->h_step += nsteps;
+    }
+    return ADS_OK;
+}
+
+int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps)
+{
+    if (!sims || count < 0) return fail(ADS_ERR_INVALID_ARG, "ads_batch_step: bad arguments");
+    for (int i = 0; i < count; ++i) {
+        int rc = ads_step(sims[i], nsteps);
+        if (rc) return rc;
+    }
+    return ADS_OK;
+}
+
+int ads_sync(ads_sim_t *s)
+{
+    if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_sync: null sim");
+    cudaSetDevice(s->device);
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    return check_device_error(s);
+}
+
+int ads_get_step(const ads_sim_t *s, long long *n)
+{
+    if (!s || !n) return fail(ADS_ERR_INVALID_ARG, "ads_get_step: null argument");
+    *n = s->h_step;
+    return ADS_OK;
+}
+
+int ads_energy(ads_sim_t *s, double *kinetic, double *potential, double *kin_mod)
+{
+    if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_energy: null sim");
+    cudaSetDevice(s->device);
+    Scratch sc(s);
+    const size_t ni = (size_t)s->d.count() * sizeof(double);
+    double *u = (double *)sc.get(ni), *v = (double *)sc.get(ni), *w = (double *)sc.get(ni), *t = (double *)sc.get(ni);
+    if (!u || !v || !w || !t) return fail(ADS_ERR_OOM, "ads_energy: scratch allocation failed");
+    int rc = s->prec == ADS_FP64 ? get_uva<double>(s, u, v, nullptr) : get_uva<float>(s, u, v, nullptr);
+    if (rc) return rc;
+    double vmv = 0, uku = 0, vgv = 0, vkv = 0;
+    if ((rc = apply_kron64(s, s->t64.M, v, w, t)) || (rc = dot64(s, v, w, &vmv))) return rc;
+    if ((rc = apply_stiff64(s, u, w)) || (rc = dot64(s, u, w, &uku))) return rc;
+    if (kin_mod) {
+        if ((rc = apply_kron64(s, s->t64.gband, v, w, t)) || (rc = dot64(s, v, w, &vgv))) return rc;
+        if ((rc = apply_stiff64(s, v, w)) || (rc = dot64(s, v, w, &vkv))) return rc;
+        *kin_mod = 0.5 * (vgv - 0.25 * s->tau * s->tau * vkv);
+    }
+    if (kinetic) *kinetic = 0.5 * vmv;
+    if (potential) *potential = 0.5 * uku;
+    return ADS_OK;
+}
+
+int ads_apply(ads_sim_t *s, int op, const double *in, double *out, size_t count, int mem)
+{
+    if (!s || !in || !out) return fail(ADS_ERR_INVALID_ARG, "ads_apply: null argument");
+    const size_t nf = (size_t)(s->d.mx + 2) * (s->d.my + 2) * (s->d.mz + 2);
+    if (count != nf) return fail(ADS_ERR_INVALID_ARG, "ads_apply: count must be n0*n1*n2");
+    if (mem != ADS_HOST && mem != ADS_DEVICE) return fail(ADS_ERR_INVALID_ARG, "ads_apply: mem");
+    if (op == ADS_OP_SPLIT_SOLVE && s->kind != ADS_SCALAR_WAVE)
+        return fail(ADS_ERR_INVALID_ARG, "ads_apply: split solve is defined for the scalar wave");
+    cudaSetDevice(s->device);
+    Scratch sc(s);
+    const size_t ni = (size_t)s->d.count() * sizeof(double);
+    double *x = (double *)sc.get(ni), *y = (double *)sc.get(ni), *t = (double *)sc.get(ni);
+    if (!x || !y || !t) return fail(ADS_ERR_OOM, "ads_apply: scratch allocation failed");
+    int rc = stage_in(s, sc, in, mem, count, x, 1.0);
+    if (rc) return rc;
+    switch (op) {
+    case ADS_OP_MASS: rc = apply_kron64(s, s->t64.M, x, y, t); break;
+    case ADS_OP_STIFF: rc = apply_stiff64(s, x, y); break;
+    case ADS_OP_MASS_SOLVE: rc = kron_solve64(s, x, SET_MASS); y = x; break;
+    case ADS_OP_SPLIT_SOLVE: rc = kron_solve64(s, x, SET_SPLIT); y = x; break;
+    default: return fail(ADS_ERR_INVALID_ARG, "ads_apply: unknown op");
+    }
+    if (rc) return rc;
+    return stage_out(s, sc, y, out, mem, count);
+}
+
+size_t ads_checkpoint_bytes(const ads_sim_t *s)
+{
+    if (!s) return 0;
+    return 3 * (size_t)s->d.count() * elem(s) + sizeof(long long);
+}
+
+int ads_checkpoint_save(ads_sim_t *s, void *host, size_t bytes)
+{
+    if (!s || !host || bytes != ads_checkpoint_bytes(s)) return fail(ADS_ERR_INVALID_ARG, "ads_checkpoint_save: bad arguments");
+    cudaSetDevice(s->device);
+    const size_t n = (size_t)s->d.count() * elem(s);
+    char *h = (char *)host;
+    ADS_CK(cudaMemcpyAsync(h, s->P, n, cudaMemcpyDeviceToHost, s->stream));
+    ADS_CK(cudaMemcpyAsync(h + n, s->Q, n, cudaMemcpyDeviceToHost, s->stream));
+    ADS_CK(cudaMemcpyAsync(h + 2 * n, s->A, n, cudaMemcpyDeviceToHost, s->stream));
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    std::memcpy(h + 3 * n, &s->h_step, sizeof(long long));
+    return ADS_OK;
+}
+
+int ads_checkpoint_load(ads_sim_t *s, const void *host, size_t bytes)
+{
+    if (!s || !host || bytes != ads_checkpoint_bytes(s)) return fail(ADS_ERR_INVALID_ARG, "ads_checkpoint_load: bad arguments");
+    cudaSetDevice(s->device);
+    const size_t n = (size_t)s->d.count() * elem(s);
+    const char *h = (const char *)host;
+    ADS_CK(cudaMemcpyAsync(s->P, h, n, cudaMemcpyHostToDevice, s->stream));
+    ADS_CK(cudaMemcpyAsync(s->Q, h + n, n, cudaMemcpyHostToDevice, s->stream));
+    ADS_CK(cudaMemcpyAsync(s->A, h + 2 * n, n, cudaMemcpyHostToDevice, s->stream));
+    std::memcpy(&s->h_step, h + 3 * n, sizeof(long long));
+    ADS_CK(cudaMemcpyAsync(s->d_step, &s->h_step, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    return ADS_OK;
+}
+
+size_t ads_device_bytes(const ads_sim_t *s) { return s ? s->bytes : 0; }
+
+int ads_profile_step(ads_sim_t *s, const char **names, float *ms, int cap, int *count)
+{
+    if (!s || !count || cap < 0) return fail(ADS_ERR_INVALID_ARG, "ads_profile_step: bad arguments");
+    cudaSetDevice(s->device);
+    KernelTimer kt;
+    int rc = s->prec == ADS_FP64 ? pwave_step<double>(s, true, &kt) : pwave_step<float>(s, true, &kt);
+    if (rc) return rc;
+    s->h_step += 1;
+    s->warmed = true;
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    const int nk = (int)kt.ev.size() - 1;
+    for (int i = 0; i < nk && i < cap; ++i) {
+        float t = 0.f;
+        ADS_CK(cudaEventElapsedTime(&t, kt.ev[i], kt.ev[i + 1]));
+        if (ms) ms[i] = t;
+        if (names) names[i] = kt.names[i];
+    }
+    *count = nk;
+    return ADS_OK;
+}
+
+}  // extern "C"

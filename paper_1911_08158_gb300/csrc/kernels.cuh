@@ -1,0 +1,140 @@
+// kernels.cuh -- launch interface of the device kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ads {
+
+// Interior field layout on the device: [z][y][x], x fastest, row pitch sx
+// elements (sx >= mx, padding kept at zero), plane pitch sx*my.
+struct Dims {
+    int mx, my, mz, sx;
+    __host__ __device__ long long plane() const { return (long long)sx * my; }
+    __host__ __device__ long long count() const { return plane() * mz; }
+};
+
+// Device tables of one directional factor set for the partitioned line
+// solve (layouts in setup1d.h): factor rows [m][2p+1], fundamental
+// solutions [m][p], transfer matrices [S][p][p], segment bounds [S+1].
+// One contiguous buffer, in this order (T elements, no gaps):
+//   fac [m_pad][2p+1] | phi [m_pad][p] | psi [m_pad][p] | Phi [S][p][p] | Psi [S][p][p]
+// with m_pad = S * SEG; segment s = rows [s*SEG, (s+1)*SEG).  It is copied
+// to shared memory verbatim (one bulk copy) by the sweep kernels.
+template <typename T>
+struct LineDev {
+    const T *base;
+    int S;
+    int bytes;            // padded to 16
+};
+
+// Operator band of one axis with its Toeplitz interior rows [lo, hi).
+template <typename T>
+struct BandDev {
+    const T *v;           // [m][2p+1]
+    int lo, hi;
+};
+
+// Source term of the scalar wave: F(t) = r(t) fx(x) fy(y) fz(z) (separable
+// Gaussian times a Ricker wavelet).  fx == nullptr means no source.
+template <typename T>
+struct SrcDev {
+    const T *fx, *fy, *fz;
+    double amp, freq, t0;
+};
+
+// Fused RHS + directional sweeps (kernel K1), one z-plane tile per CTA:
+//   out = Ax^{-1} [ F(t) - c2 (Kx.My.Mz + Mx.Ky.Mz + Mx.My.Kz) in ]   (along x)
+// and, when the tile spans all of y (ty == my), also Ay^{-1} along y.
+// t = (step[0] + toff) * tau.
+template <typename T>
+struct RhsArgs {
+    const T *in;
+    T *out;
+    Dims d;
+    BandDev<T> bandM[3], bandK[3];
+    LineDev<T> lx, ly;
+    // shared-memory image of all 1D tables of this launch (see rhs_image_layout):
+    //   bMx bKx [mxp][W] | bMy bKy [myp][W] | fx [mxp] | fy [myp] | lx tables | ly tables
+    const T *img;
+    int img_bytes;
+    T c2;
+    SrcDev<T> src;
+    const long long *step;
+    int toff;
+    double tau;
+    int ty;               // rows per tile (y); fused y sweep iff ty == my
+    int *err;             // device error word (bounded waits)
+};
+
+// Column sweep along y (axis 1) or z (axis 2): 32 x-columns per CTA, one
+// warp per line segment.
+//   mode 0: out = A^{-1} in along the axis (in == out allowed)
+//   mode 1 (Newmark epilogue, scalar wave state p,q,a):
+//        a = A^{-1} in;  q += tau^2 a;  p += q;  a_out = a (if write_a)
+//        and step[0] += 1 (one thread)
+template <typename T>
+struct ColArgs {
+    const T *in;
+    T *out;
+    Dims d;
+    int axis;
+    LineDev<T> ln;
+    int mode;
+    T *P, *Q, *A;
+    T tau2;
+    int write_a;
+    long long *step;
+    int *err;             // device error word (bounded waits)
+};
+
+// seg: register segment width of the partitioned solves (32)
+size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy);
+int rhs_threads(int elem);
+// element offsets of the K1 table image: returns total elements
+size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy);
+size_t line_image_elems(int p, int S);
+size_t col_smem_bytes(int p, int elem, int len, int S);
+
+template <typename T>
+cudaError_t launch_rhs(int p, int seg, const RhsArgs<T> &a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_col(int p, int seg, const ColArgs<T> &a, cudaStream_t s);
+
+// out = band applied along axis (0,1,2) to in; out = beta*out + alpha*(A in)
+template <typename T>
+cudaError_t launch_axis_apply(int p, const T *band, int axis, const T *in, T *out, Dims d, T alpha, T beta,
+                              int transpose, cudaStream_t s);
+// in-place line solve along x with a factor table [m][2p+1] (thread per line)
+template <typename T>
+cudaError_t launch_solve_x(int p, const T *fac, T *data, Dims d, cudaStream_t s);
+
+// full FP64 [nz][ny][nx] <-> interior T
+template <typename T>
+cudaError_t launch_pack(const double *full, T *in, Dims d, double scale, cudaStream_t s);
+template <typename T>
+cudaError_t launch_unpack(const T *in, double *full, Dims d, cudaStream_t s);
+// convert between (u, v, a) FP64 interior and (p, q, a) T:
+//   p = u + tau v + tau^2/4 a,  q = tau v + tau^2/2 a
+template <typename T>
+cudaError_t launch_uva_to_pq(const double *u, const double *v, const double *a, T *P, T *Q, T *A, Dims d,
+                             double tau, cudaStream_t s);
+//   u = p - q + tau^2/4 a,  v = (q - tau^2/2 a) / tau
+template <typename T>
+cudaError_t launch_pq_to_uva(const T *P, const T *Q, const T *A, double *u, double *v, double *a, Dims d,
+                             double tau, cudaStream_t s);
+// out = amp * gz[z] gy[y] gx[x]
+cudaError_t launch_outer(const double *gx, const double *gy, const double *gz, double amp, double *out, Dims d,
+                         cudaStream_t s);
+// y = a*x + b*y (FP64, interior incl. padding)
+cudaError_t launch_axpby(double a, const double *x, double b, double *y, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert(const T *x, double *y, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert_from(const double *x, T *y, long long n, cudaStream_t s);
+// partial[block] = compensated sum of x*y; then a 1-block pass -> result[0]
+cudaError_t launch_dot(const double *x, const double *y, long long n, double *partial, int nblocks,
+                       double *result, cudaStream_t s);
+
+extern unsigned long long g_launches;
+
+}  // namespace ads

@@ -1,0 +1,50 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/ads.h declares (no compute calls: runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(ads_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_1911_08158_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_last_error_and_launch_count_without_gpu():
+    import paper_1911_08158_gb300 as ads
+    L = ads.library()
+    assert L.ads_launch_count() >= 0
+    assert isinstance(L.ads_last_error(), bytes)
+
+
+def test_invalid_arguments_rejected_on_host():
+    import paper_1911_08158_gb300 as ads
+    # p out of range is rejected before any device call
+    with pytest.raises(ads.AdsError) as e:
+        ads.Simulation(4, 7, 0.01, use_torch=False)
+    assert e.value.code == -5
+    with pytest.raises(ads.AdsError) as e:
+        ads.Simulation(4, 2, -1.0, use_torch=False)
+    assert e.value.code == -1
+    with pytest.raises(ads.AdsError) as e:
+        ads.Simulation((4, 0, 4), 2, 0.01, use_torch=False)
+    assert e.value.code == -1
