@@ -181,6 +181,24 @@ int ads_energy(ads_sim_t *sim, double *kinetic, double *potential, double *kin_m
  * scalar field (count = n0*n1*n2 doubles), in FP64 on the device.  Waits. */
 int ads_apply(ads_sim_t *sim, int op, const double *in, double *out, size_t count, int mem);
 
+/* ads_apply for callers that must not allocate device memory while they
+ * run (for example code issuing work while a stream is being captured into
+ * a CUDA graph, or a loop whose memory is fixed up front).  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ *   in, out: DEVICE pointers to FP64 fields of the full space (count =
+ *            n0*n1*n2, boundary coefficients ignored / written as zero).
+ *   Scratch: a fixed array compiled into the library, two fields of at most
+ *            524288 doubles each (8 MiB, held by every GPU that loads the
+ *            library until the process exits); spaces whose padded interior
+ *            is larger are rejected with ADS_ERR_UNSUPPORTED.  No cudaMalloc,
+ *            cudaFree or allocating library routine is called.
+ *   The first call on a device resolves the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (two
+ *   streams, two simulations at once) race; serialise them.  Waits for the
+ *   simulation's stream. */
+int ads_apply_noalloc(ads_sim_t *sim, int op, const double *in, double *out, size_t count);
+
 /* Checkpoint: the raw device state (all precisions bit-exact) plus the
  * step counter.  bytes = ads_checkpoint_bytes(); save waits for the stream. */
 size_t ads_checkpoint_bytes(const ads_sim_t *sim);

@@ -88,6 +88,7 @@ def library() -> ctypes.CDLL:
         L.ads_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.ads_energy.argtypes = [vp, _D, _D, _D]
         L.ads_apply.argtypes = [vp, i, vp, vp, sz, i]
+        L.ads_apply_noalloc.argtypes = [vp, i, vp, vp, sz]
         L.ads_checkpoint_bytes.argtypes = [vp]
         L.ads_checkpoint_bytes.restype = sz
         L.ads_checkpoint_save.argtypes = [vp, vp, sz]
@@ -294,6 +295,16 @@ class Simulation:
         out = np.zeros_like(x)
         _check(library().ads_apply(self._h, int(op), x.ctypes.data, out.ctypes.data, n1, ADS_HOST))
         return out
+
+    def apply_noalloc(self, op: int, x, out):
+        """ads_apply_noalloc on CUDA float64 tensors of the full scalar space
+        (no device allocation inside the call)."""
+        n1 = int(np.prod(self.n))
+        px, mx_, _ = _ptr(x, n1)
+        po, mo, _ = _ptr(out, n1)
+        if mx_ != ADS_DEVICE or mo != ADS_DEVICE:
+            raise ValueError("apply_noalloc takes CUDA tensors")
+        _check(library().ads_apply_noalloc(self._h, int(op), px, po, n1))
 
     def checkpoint(self) -> bytes:
         L = library()

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libads_gb300.so")
-SOURCES = ["kernels.cu", "api.cpp", "setup1d.cpp"]
+SOURCES = ["kernels.cu", "api.cpp", "setup1d.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "internal.h"
 #include "kernels.cuh"
 #include "setup1d.h"
 
@@ -1014,6 +1015,50 @@ int ads_checkpoint_load(ads_sim_t *s, const void *host, size_t bytes)
 }
 
 size_t ads_device_bytes(const ads_sim_t *s) { return s ? s->bytes : 0; }
+
+}  // extern "C"
+
+size_t ads_internal_interior_count(const ads_sim_t *s) { return s ? (size_t)s->d.count() : 0; }
+
+int ads_internal_sim_device(const ads_sim_t *s) { return s ? s->device : 0; }
+
+int ads_internal_fail(int code, const char *msg) { return fail(code, msg); }
+
+int ads_internal_apply_scratch(ads_sim_t *s, int op, const double *in, double *out, size_t count, double *s0,
+                               double *s1)
+{
+    if (!s || !in || !out || !s0 || !s1) return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: null argument");
+    const size_t nf = (size_t)(s->d.mx + 2) * (s->d.my + 2) * (s->d.mz + 2);
+    if (count != nf) return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: count must be n0*n1*n2");
+    if (op == ADS_OP_SPLIT_SOLVE && s->kind != ADS_SCALAR_WAVE)
+        return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: split solve is defined for the scalar wave");
+    cudaSetDevice(s->device);
+    // interior scratch starts from zero (padding columns are read as zeros)
+    ADS_CK(cudaMemsetAsync(s0, 0, (size_t)s->d.count() * sizeof(double), s->stream));
+    ADS_CK(cudaMemsetAsync(s1, 0, (size_t)s->d.count() * sizeof(double), s->stream));
+    ADS_CK(ads::launch_pack<double>(in, s0, s->d, 1.0, s->stream));
+    int rc;
+    double *res = s1;
+    switch (op) {
+    case ADS_OP_MASS:
+        // s0 -> s1 -> s0 -> s1 along x, y, z
+        ADS_CK(ads::launch_axis_apply<double>(s->p, (const double *)s->t64.M[0], 0, s0, s1, s->d, 1.0, 0.0, 0, s->stream));
+        ADS_CK(ads::launch_axis_apply<double>(s->p, (const double *)s->t64.M[1], 1, s1, s0, s->d, 1.0, 0.0, 0, s->stream));
+        ADS_CK(ads::launch_axis_apply<double>(s->p, (const double *)s->t64.M[2], 2, s0, s1, s->d, 1.0, 0.0, 0, s->stream));
+        rc = ADS_OK;
+        break;
+    case ADS_OP_STIFF: rc = apply_stiff64(s, s0, s1); break;
+    case ADS_OP_MASS_SOLVE: rc = kron_solve64(s, s0, SET_MASS); res = s0; break;
+    case ADS_OP_SPLIT_SOLVE: rc = kron_solve64(s, s0, SET_SPLIT); res = s0; break;
+    default: return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: unknown op");
+    }
+    if (rc) return rc;
+    ADS_CK(ads::launch_unpack<double>(res, out, s->d, s->stream));
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    return check_device_error(s);
+}
+
+extern "C" {
 
 int ads_profile_step(ads_sim_t *s, const char **names, float *ms, int cap, int *count)
 {
