@@ -82,6 +82,12 @@ def lib():
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _D]
             L.ora_elastic_start.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _D, _D, _D]
+            L.ora_elastic_run_src.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _D, _D, _D,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_long]
+            L.ora_elastic_start_src.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.ora_elastic_invariant.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_double, _D, _D]
             L.ora_elastic_invariant.restype = ctypes.c_double
@@ -251,15 +257,28 @@ class Space:
         lib().ora_elastic_apply(self._h, lam, mu, _p(U), _p(out))
         return out
 
-    def elastic_start(self, tau, lam, mu, rho, U0, V0):
+    def elastic_start(self, tau, lam, mu, rho, U0, V0, G=None, direction=None, rick=(8.0, 0.125), t0=0.0):
         U0, V0 = _cont(U0), _cont(V0)
         Up = np.zeros_like(U0)
-        lib().ora_elastic_start(self._h, tau, lam, mu, rho, _p(U0), _p(V0), _p(Up))
+        if G is None:
+            lib().ora_elastic_start(self._h, tau, lam, mu, rho, _p(U0), _p(V0), _p(Up))
+        else:
+            G, d = _cont(G), _cont(direction)
+            lib().ora_elastic_start_src(self._h, tau, lam, mu, rho, _p(U0), _p(V0), _p(Up), _p(G), _p(d),
+                                        rick[0], rick[1], t0)
         return Up
 
-    def elastic_run(self, tau, lam, mu, rho, nsteps, Ucur, Uprev):
+    def elastic_run(self, tau, lam, mu, rho, nsteps, Ucur, Uprev, G=None, direction=None, rick=(8.0, 0.125),
+                    step0=0):
+        """Advance (U^n, U^{n-1}) by nsteps; G, direction: body force
+        f^n = ricker(t_n) direction_i G at level n (t_n = n tau)."""
         Ucur, Uprev = _cont(Ucur).copy(), _cont(Uprev).copy()
-        lib().ora_elastic_run(self._h, tau, lam, mu, rho, nsteps, _p(Ucur), _p(Uprev))
+        if G is None:
+            lib().ora_elastic_run(self._h, tau, lam, mu, rho, nsteps, _p(Ucur), _p(Uprev))
+        else:
+            G, d = _cont(G), _cont(direction)
+            lib().ora_elastic_run_src(self._h, tau, lam, mu, rho, nsteps, _p(Ucur), _p(Uprev), _p(G), _p(d),
+                                      rick[0], rick[1], step0)
         return Ucur, Uprev
 
     def elastic_invariant(self, tau, lam, mu, rho, U1, U):

@@ -620,8 +620,22 @@ static void elastic_diag_solve(const ora_space *s, double tau, double lam, doubl
  *   D (U1 - 2U + U0) / tau^2 + Upsilon U = f,  f = 0 here,
  *   D = (rho M + tau^2/2 Ups1~) (rho M)^{-1} (rho M + tau^2/2 Ups2~).
  * Block-lower solve for y, y -> rho M y, block-upper solve for delta. */
+void ora_elastic_run_src(const ora_space *s, double tau, double lam, double mu, double rho, int nsteps,
+                         double *Ucur, double *Uprev, const double *G, const double *dir, double rf, double rt0,
+                         long step0);
+
 void ora_elastic_run(const ora_space *s, double tau, double lam, double mu, double rho, int nsteps,
                      double *Ucur, double *Uprev)
+{
+    ora_elastic_run_src(s, tau, lam, mu, rho, nsteps, Ucur, Uprev, NULL, NULL, 0.0, 0.0, 0);
+}
+
+/* As ora_elastic_run with a body force f^n = r(t_n) dir_i g (eq. gen: the
+ * right-hand side at level n, t_n = n tau), G = (g, w) the scalar load;
+ * G == NULL: no force.  step0 = index n of Ucur. */
+void ora_elastic_run_src(const ora_space *s, double tau, double lam, double mu, double rho, int nsteps,
+                         double *Ucur, double *Uprev, const double *G, const double *dir, double rf, double rt0,
+                         long step0)
 {
     size_t N = ora_size(s);
     double *r = (double *)malloc(sizeof(double) * 3 * N);
@@ -634,6 +648,11 @@ void ora_elastic_run(const ora_space *s, double tau, double lam, double mu, doub
     for (int n = 0; n < nsteps; n++) {
         ora_elastic_apply(s, lam, mu, Ucur, r);
         for (size_t k = 0; k < 3 * N; k++) r[k] = -tau * tau * r[k];
+        if (G) {
+            const double rt = ora_ricker(rf, rt0, (double)(step0 + n) * tau);
+            for (int i = 0; i < 3; i++)
+                for (size_t k = 0; k < N; k++) r[i * N + k] += tau * tau * rt * dir[i] * G[k];
+        }
         /* block lower: for i = x, y, z */
         for (int i = 0; i < 3; i++) {
             memcpy(rhs, r + i * N, sizeof(double) * N);
@@ -670,15 +689,29 @@ void ora_elastic_run(const ora_space *s, double tau, double lam, double mu, doub
 
 /* Start-up of the three-level scheme: U^{-1} = U0 - tau V0 + tau^2/2 A0 with
  * A0 = (rho M)^{-1}(f - Upsilon U0), f = 0. */
+void ora_elastic_start_src(const ora_space *s, double tau, double lam, double mu, double rho, const double *U0,
+                           const double *V0, double *Uprev, const double *G, const double *dir, double rf, double rt0,
+                           double t0);
+
 void ora_elastic_start(const ora_space *s, double tau, double lam, double mu, double rho, const double *U0,
                        const double *V0, double *Uprev)
+{
+    ora_elastic_start_src(s, tau, lam, mu, rho, U0, V0, Uprev, NULL, NULL, 0.0, 0.0, 0.0);
+}
+
+/* start-up with a body force f(t0) = r(t0) dir_i g */
+void ora_elastic_start_src(const ora_space *s, double tau, double lam, double mu, double rho, const double *U0,
+                           const double *V0, double *Uprev, const double *G, const double *dir, double rf, double rt0,
+                           double t0)
 {
     size_t N = ora_size(s);
     double *r = (double *)malloc(sizeof(double) * 3 * N);
     double *A0 = (double *)malloc(sizeof(double) * 3 * N);
     ora_elastic_apply(s, lam, mu, U0, r);
+    const double rt = G ? ora_ricker(rf, rt0, t0) : 0.0;
     for (int i = 0; i < 3; i++) {
-        for (size_t k = 0; k < N; k++) r[i * N + k] = -r[i * N + k] / rho;
+        for (size_t k = 0; k < N; k++)
+            r[i * N + k] = ((G ? rt * dir[i] * G[k] : 0.0) - r[i * N + k]) / rho;
         ora_solve_mass(s, r + i * N, A0 + i * N);
     }
     for (size_t k = 0; k < 3 * N; k++) Uprev[k] = U0[k] - tau * V0[k] + 0.5 * tau * tau * A0[k];

@@ -122,3 +122,24 @@ def test_atm_second_order_in_time():
     errs = [np.linalg.norm(run(N) - ref_u) for N in (20, 40, 80)]
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(rates - 2.0) < 0.15), rates
+
+
+def test_atm_body_force_enters_at_level_n():
+    """eq. gen: D (U^{n+1} - 2U^n + U^{n-1}) / tau^2 + Ups U^n = f^n, with
+    f^n = r(t_n) dir g; from a zero state one step gives D delta = tau^2 f^n."""
+    p, lam, mu, rho, tau = 2, 1.3, 0.8, 1.1, 0.04
+    s = ora.Space(NE, p)
+    S = ref.elastic_dense(NE, p, lam, mu)
+    Lo, Up, RM = _dense_atm(s, S, tau, lam, mu, rho)
+    D = Lo @ np.linalg.solve(RM, Up)
+    G = s.load_gauss(1.0, (0.4, 0.5, 0.6), 0.05)
+    d = np.array([0.3, -0.5, 0.8])
+    z = s.zeros(3)
+    U1, _ = s.elastic_run(tau, lam, mu, rho, 1, z, z, G=G, direction=d, rick=(8.0, 0.125), step0=5)
+    f = ora.ricker(8.0, 0.125, 5 * tau) * np.concatenate([d[i] * G.ravel() for i in range(3)])
+    np.testing.assert_allclose(U1.ravel(), np.linalg.solve(D, tau ** 2 * f), rtol=1e-9, atol=1e-14)
+    # start-up with a force: U^{-1} = U0 - tau V0 + tau^2/2 (rho M)^{-1} f(t0)
+    Um = s.elastic_start(tau, lam, mu, rho, z, z, G=G, direction=d, rick=(8.0, 0.125), t0=0.0)
+    M3 = np.kron(np.eye(3), rho * ref.kron3(*[s.mat(a, "M") for a in range(3)]))
+    f0 = ora.ricker(8.0, 0.125, 0.0) * np.concatenate([d[i] * G.ravel() for i in range(3)])
+    np.testing.assert_allclose(Um.ravel(), 0.5 * tau ** 2 * np.linalg.solve(M3, f0), rtol=1e-9, atol=1e-16)
