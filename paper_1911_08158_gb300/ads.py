@@ -251,8 +251,11 @@ class Simulation:
             raise ValueError("u, v, a must all be host or all device arrays")
         _check(library().ads_set_state(self._h, pu, pv, pa, self.count, mu_))
 
-    def get_state(self, out=None, fields=("u", "v", "a")):
-        """Returns (u, v, a) as NumPy arrays (None for fields not requested)."""
+    def get_state(self, out=None, fields=None):
+        """Returns (u, v, a) as NumPy arrays (None for fields not requested;
+        elasticity has no a: v = (U^n - U^{n-1})/tau)."""
+        if fields is None:
+            fields = ("u", "v") if self.comps == 3 else ("u", "v", "a")
         arrs = {}
         ptrs = []
         for f in ("u", "v", "a"):

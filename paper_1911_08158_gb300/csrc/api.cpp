@@ -79,6 +79,9 @@ struct ads_sim {
     int lineS[3] = {0, 0, 0};
     // scalar-wave state (precision prec): p = u + tau v + eta a, q = tau v + tau^2/2 a
     void *P = nullptr, *Q = nullptr, *A = nullptr, *X = nullptr;
+    // elasticity state: U^n, U^{n-1} (3 components, component-major) and work
+    void *U = nullptr, *Up = nullptr, *R = nullptr, *Y = nullptr, *T1 = nullptr, *T2 = nullptr;
+    void *ebandFP64[3][2] = {};   // bands of M + d K (d = tau^2 c / (4 rho)), FP64, for the invariant
     long long *d_step = nullptr;
     long long h_step = 0;
     int *d_err = nullptr;   // device error word written by bounded waits
@@ -87,8 +90,9 @@ struct ads_sim {
     // kernel tiling of K1 per precision
     int ty[2] = {0, 0}, tz[2] = {0, 0}, fuse[2] = {0, 0};
     int seg = 32;           // register segment width of the line solves
-    // graphs: chunk size -> executable graph
+    // graphs: chunk size -> executable graph, and the kernels it launches
     std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, unsigned long long> graph_launches;
     bool warmed = false;
 };
 
@@ -421,17 +425,22 @@ int apply_kron64(ads_sim *s, void *const *band, const double *in, double *out, d
     return ADS_OK;
 }
 
-int dot64(ads_sim *s, const double *x, const double *y, double *result_host)
+int dot64_n(ads_sim *s, const double *x, const double *y, long long n, double *result_host)
 {
     Scratch sc(s);
     const int nb = 304;
     double *part = (double *)sc.get(sizeof(double) * 2 * nb + sizeof(double));
     if (!part) return fail(ADS_ERR_OOM, "scratch allocation failed");
     double *res = part + 2 * nb;
-    ADS_CK(ads::launch_dot(x, y, s->d.count(), part, nb, res, s->stream));
+    ADS_CK(ads::launch_dot(x, y, n, part, nb, res, s->stream));
     ADS_CK(cudaMemcpyAsync(result_host, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     ADS_CK(cudaStreamSynchronize(s->stream));
     return ADS_OK;
+}
+
+int dot64(ads_sim *s, const double *x, const double *y, double *result_host)
+{
+    return dot64_n(s, x, y, s->d.count(), result_host);
 }
 
 // stage a full FP64 field (host or device) into an interior FP64 array
@@ -560,8 +569,177 @@ int pwave_step(ads_sim *s, bool write_a, KernelTimer *kt = nullptr)
     return ADS_OK;
 }
 
+// ------------------------------------------------------------------ elasticity
+// Blocks of Upsilon with the Dirichlet restriction (B^T = -B on the interior):
+//   Ups_ii = mu (Kx My Mz + Mx Ky Mz + Mx My Kz) + (mu + lam) [K on axis i]
+//   Ups_ij = -(mu + lam) [B on axis i, B on axis j, M on the third],  i != j
+// (bilinear form 2 mu e(w):e(u) + lam div w div u, Sec. 5).
+
+// out = (beta ? out : 0) + coef (A0 (x) A1 (x) A2) in; which[a]: 0 = M, 1 = K, 2 = B
+template <typename T>
+int kron3(ads_sim *s, const T *in, T *out, const int *which, T coef, bool accumulate, T *ta, T *tb)
+{
+    const TableSet &ts = tables_for<T>(s);
+    const void *band[3];
+    for (int a = 0; a < 3; ++a) band[a] = which[a] == 0 ? ts.M[a] : (which[a] == 1 ? ts.K[a] : ts.B[a]);
+    ADS_CK(ads::launch_axis_apply<T>(s->p, (const T *)band[0], 0, in, ta, s->d, T(1), T(0), 0, s->stream));
+    ADS_CK(ads::launch_axis_apply<T>(s->p, (const T *)band[1], 1, ta, tb, s->d, T(1), T(0), 0, s->stream));
+    ADS_CK(ads::launch_axis_apply<T>(s->p, (const T *)band[2], 2, tb, out, s->d, coef, accumulate ? T(1) : T(0), 0,
+                                     s->stream));
+    return ADS_OK;
+}
+
+// out_i = (Ups U)_i, i = 0..2 (component stride cnt)
+template <typename T>
+int apply_upsilon(ads_sim *s, const T *U, T *out, T *ta, T *tb)
+{
+    const long long cnt = s->d.count();
+    const T lm = (T)(s->lam + s->mu);
+    for (int i = 0; i < 3; ++i) {
+        T *oi = out + i * cnt;
+        // mu K_lap U_i through K1 with identity factors: K1 returns -c2 K in
+        ads::RhsArgs<T> r = rhs_args<T>(s, U + i * cnt, oi, SET_IDENT, 0, false);
+        r.c2 = (T)(-s->mu);
+        ADS_CK(ads::launch_rhs<T>(s->p, s->seg, r, s->stream));
+        int w[3] = {0, 0, 0};
+        w[i] = 1;
+        int rc = kron3<T>(s, U + i * cnt, oi, w, lm, true, ta, tb);
+        if (rc) return rc;
+        for (int j = 0; j < 3; ++j) {
+            if (j == i) continue;
+            int b[3] = {0, 0, 0};
+            b[i] = 2;
+            b[j] = 2;
+            if ((rc = kron3<T>(s, U + j * cnt, oi, b, (T)(-lm), true, ta, tb))) return rc;
+        }
+    }
+    return ADS_OK;
+}
+
+// data <- (x)_xi (M_xi + d_i,xi K_xi)^{-1} data, d = tau^2 c_i,xi / (4 rho),
+// c_i,xi = 2 mu + lam on axis i, mu otherwise (eq. spill)
+template <typename T>
+int elastic_diag_solve(ads_sim *s, int i, T *data)
+{
+    const TableSet &ts = tables_for<T>(s);
+    auto set = [&](int a) { return a == i ? SET_ELAS0 : SET_ELAS1; };
+    ADS_CK(ads::launch_solve_x<T>(s->p, (const T *)ts.line[set(0)][0].base, data, s->d, s->stream));
+    ads::ColArgs<T> c{};
+    c.d = s->d;
+    c.mode = 0;
+    c.in = data;
+    c.out = data;
+    c.err = s->d_err;
+    c.axis = 1;
+    c.ln = line_dev<T>(ts.line[set(1)][1]);
+    ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    c.axis = 2;
+    c.ln = line_dev<T>(ts.line[set(2)][2]);
+    ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    return ADS_OK;
+}
+
+// r_i += tau^2 dir_i r(t_{n+toff}) F  (body force at level n)
+template <typename T>
+int add_body_force(ads_sim *s, T *r, double scale, int toff)
+{
+    if (!s->has_src) return ADS_OK;
+    const TableSet &ts = tables_for<T>(s);
+    const long long cnt = s->d.count();
+    for (int i = 0; i < 3; ++i) {
+        const double di = s->src.shape.dir[i];
+        if (di == 0.0) continue;
+        ADS_CK(ads::launch_add_source<T>(r + i * cnt, s->d, (const T *)ts.src[0], (const T *)ts.src[1],
+                                         (const T *)ts.src[2], scale * di, s->src.freq, s->src.t0, s->d_step, toff,
+                                         s->tau, s->stream));
+    }
+    return ADS_OK;
+}
+
+// One alternating-triangular step (eqs. decom, pre, corr, spill, gen with
+// sigma = 1/2):  D delta = tau^2 (f^n - Ups U^n),
+//   D = (rho M + tau^2/2 Ups1~) (rho M)^{-1} (rho M + tau^2/2 Ups2~),
+// block-lower solve, rho M, block-upper solve, U^{n+1} = 2U^n - U^{n-1} + delta.
+template <typename T>
+int elastic_step(ads_sim *s, KernelTimer *kt = nullptr)
+{
+    const long long cnt = s->d.count();
+    T *U = (T *)s->U, *Up = (T *)s->Up, *R = (T *)s->R, *Y = (T *)s->Y, *t1 = (T *)s->T1, *t2 = (T *)s->T2;
+    const T tau2 = (T)(s->tau * s->tau), rho = (T)s->rho;
+    const T half = (T)(0.5 * s->tau * s->tau * (s->lam + s->mu) / s->rho);   // (1/2) tau^2 (mu+lam) / rho
+    int rc;
+    if (kt && (rc = kt->mark(s->stream, "elastic_rhs"))) return rc;
+    if ((rc = apply_upsilon<T>(s, U, R, t1, t2))) return rc;
+    ADS_CK(ads::launch_lincomb<T>(R, -tau2, R, T(0), (const T *)nullptr, 3 * cnt, s->stream));
+    if ((rc = add_body_force<T>(s, R, s->tau * s->tau, 0))) return rc;
+    if (kt && (rc = kt->mark(s->stream, "elastic_lower"))) return rc;
+    // lower: y_i = L~_i^{-1} (r_i - tau^2/2 sum_{j<i} Ups_ij y_j)
+    for (int i = 0; i < 3; ++i) {
+        T *yi = Y + i * cnt;
+        ADS_CK(ads::launch_lincomb<T>(yi, T(1) / rho, R + i * cnt, T(0), (const T *)nullptr, cnt, s->stream));
+        for (int j = 0; j < i; ++j) {
+            int b[3] = {0, 0, 0};
+            b[i] = 2;
+            b[j] = 2;
+            if ((rc = kron3<T>(s, Y + j * cnt, yi, b, half, true, t1, t2))) return rc;
+        }
+        if ((rc = elastic_diag_solve<T>(s, i, yi))) return rc;
+    }
+    if (kt && (rc = kt->mark(s->stream, "elastic_mass"))) return rc;
+    // s = rho M y  (into R)
+    for (int i = 0; i < 3; ++i) {
+        const int m3[3] = {0, 0, 0};
+        if ((rc = kron3<T>(s, Y + i * cnt, R + i * cnt, m3, rho, false, t1, t2))) return rc;
+    }
+    if (kt && (rc = kt->mark(s->stream, "elastic_upper"))) return rc;
+    // upper: delta_i = L~_i^{-1} (s_i - tau^2/2 sum_{j>i} Ups_ij delta_j), delta stored in Y
+    for (int i = 2; i >= 0; --i) {
+        T *yi = Y + i * cnt;
+        ADS_CK(ads::launch_lincomb<T>(yi, T(1) / rho, R + i * cnt, T(0), (const T *)nullptr, cnt, s->stream));
+        for (int j = i + 1; j < 3; ++j) {
+            int b[3] = {0, 0, 0};
+            b[i] = 2;
+            b[j] = 2;
+            if ((rc = kron3<T>(s, Y + j * cnt, yi, b, half, true, t1, t2))) return rc;
+        }
+        if ((rc = elastic_diag_solve<T>(s, i, yi))) return rc;
+    }
+    if (kt && (rc = kt->mark(s->stream, "elastic_update"))) return rc;
+    ADS_CK(ads::launch_atm_update<T>(U, Up, Y, 3 * cnt, s->d_step, s->stream));
+    if (kt && (rc = kt->mark(s->stream, ""))) return rc;
+    return ADS_OK;
+}
+
+// U^{-1} = U0 - tau V0 + tau^2/2 A0,  A0 = (rho M)^{-1}(f(t_n) - Ups U0)   (FP64)
+int elastic_set64(ads_sim *s, Scratch &sc, const double *U0, const double *V0)
+{
+    const long long cnt = s->d.count();
+    const size_t bytes = (size_t)cnt * sizeof(double);
+    double *A = (double *)sc.get(3 * bytes), *t1 = (double *)sc.get(bytes), *t2 = (double *)sc.get(bytes);
+    double *Upv = (double *)sc.get(3 * bytes);
+    if (!A || !t1 || !t2 || !Upv) return fail(ADS_ERR_OOM, "scratch allocation failed");
+    int rc;
+    if ((rc = apply_upsilon<double>(s, U0, A, t1, t2))) return rc;
+    ADS_CK(ads::launch_lincomb<double>(A, -1.0, A, 0.0, nullptr, 3 * cnt, s->stream));
+    if ((rc = add_body_force<double>(s, A, 1.0, 0))) return rc;
+    for (int i = 0; i < 3; ++i)
+        if ((rc = kron_solve64(s, A + i * cnt, SET_MASS))) return rc;
+    // Up = U0 - tau V0 + tau^2/(2 rho) A
+    ADS_CK(ads::launch_lincomb<double>(Upv, 1.0, U0, -s->tau, V0, 3 * cnt, s->stream));
+    ADS_CK(ads::launch_lincomb<double>(Upv, 1.0, Upv, 0.5 * s->tau * s->tau / s->rho, A, 3 * cnt, s->stream));
+    if (s->prec == ADS_FP64) {
+        ADS_CK(cudaMemcpyAsync(s->U, U0, 3 * bytes, cudaMemcpyDeviceToDevice, s->stream));
+        ADS_CK(cudaMemcpyAsync(s->Up, Upv, 3 * bytes, cudaMemcpyDeviceToDevice, s->stream));
+    } else {
+        ADS_CK(ads::launch_convert_from<float>(U0, (float *)s->U, 3 * cnt, s->stream));
+        ADS_CK(ads::launch_convert_from<float>(Upv, (float *)s->Up, 3 * cnt, s->stream));
+    }
+    return ADS_OK;
+}
+
 int step_once(ads_sim *s, bool write_a)
 {
+    if (s->kind == ADS_ELASTIC) return s->prec == ADS_FP64 ? elastic_step<double>(s) : elastic_step<float>(s);
     return s->prec == ADS_FP64 ? pwave_step<double>(s, write_a) : pwave_step<float>(s, write_a);
 }
 
@@ -578,6 +756,7 @@ int get_graph(ads_sim *s, int chunk, cudaGraphExec_t *out)
     int rc = ADS_OK;
     for (int i = 0; i < chunk && rc == ADS_OK; ++i) rc = step_once(s, i == chunk - 1);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    s->graph_launches[chunk] = ads::g_launches - before;   // kernels recorded in the graph
     ads::g_launches = before;
     if (rc != ADS_OK) {
         if (g) cudaGraphDestroy(g);
@@ -604,16 +783,69 @@ int rebuild_images(ads_sim *s)
     }
     for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
     s->graphs.clear();
+    s->graph_launches.clear();
     return ADS_OK;
 }
 
-int launches_per_step(const ads_sim *s)
-{
-    const int pi = s->prec == ADS_FP64 ? 0 : 1;
-    return s->fuse[pi] ? 2 : 3;
-}
-
 }  // namespace
+
+// Energies of the elastic state (FP64): kinetic 1/2 rho V^T M V with
+// V = (U^n - U^{n-1})/tau, potential 1/2 U^T Ups U, and the discrete
+// invariant of the three-level scheme at n-1/2 (f = 0):
+//   E = |V|^2_{D - tau^2 Ups/4} + |(U^n + U^{n-1})/2|^2_Ups,
+//   |x|^2_D = (L^T x)^T (rho M)^{-1} (L^T x), L^T the block-upper factor.
+int elastic_energy(ads_sim *s, double *kinetic, double *potential, double *kin_mod)
+{
+    Scratch sc(s);
+    const long long cnt = s->d.count();
+    const size_t b1 = (size_t)cnt * sizeof(double), b3 = 3 * b1;
+    double *u = (double *)sc.get(b3), *v = (double *)sc.get(b3), *w = (double *)sc.get(b3), *z = (double *)sc.get(b3);
+    double *t1 = (double *)sc.get(b1), *t2 = (double *)sc.get(b1);
+    if (!u || !v || !w || !z || !t1 || !t2) return fail(ADS_ERR_OOM, "ads_energy: scratch allocation failed");
+    if (s->prec == ADS_FP64)
+        ADS_CK(ads::launch_el_to_uv<double>((const double *)s->U, (const double *)s->Up, u, v, 3 * cnt, s->tau,
+                                            s->stream));
+    else
+        ADS_CK(ads::launch_el_to_uv<float>((const float *)s->U, (const float *)s->Up, u, v, 3 * cnt, s->tau,
+                                           s->stream));
+    auto dot3 = [&](const double *x, const double *y, double *out) { return dot64_n(s, x, y, 3 * cnt, out); };
+    int rc;
+    double vmv = 0, uuu = 0;
+    for (int i = 0; i < 3; ++i)
+        if ((rc = apply_kron64(s, s->t64.M, v + i * cnt, w + i * cnt, t1))) return rc;
+    if ((rc = dot3(v, w, &vmv))) return rc;
+    if ((rc = apply_upsilon<double>(s, u, w, t1, t2)) || (rc = dot3(u, w, &uuu))) return rc;
+    if (kinetic) *kinetic = 0.5 * s->rho * vmv;
+    if (potential) *potential = 0.5 * uuu;
+    if (!kin_mod) return ADS_OK;
+    // w = L^T v: rho (x)(M + d K) v_i  - tau^2/2 (mu+lam) sum_{j>i} [B_i B_j M] v_j
+    const double half = 0.5 * s->tau * s->tau * (s->lam + s->mu);
+    for (int i = 0; i < 3; ++i) {
+        void *eb[3];
+        for (int a = 0; a < 3; ++a) eb[a] = s->ebandFP64[a][a == i ? 0 : 1];
+        if ((rc = apply_kron64(s, eb, v + i * cnt, w + i * cnt, t1))) return rc;
+        ADS_CK(ads::launch_lincomb<double>(w + i * cnt, s->rho, w + i * cnt, 0.0, nullptr, cnt, s->stream));
+        for (int j = i + 1; j < 3; ++j) {
+            int b[3] = {0, 0, 0};
+            b[i] = 2;
+            b[j] = 2;
+            if ((rc = kron3<double>(s, v + j * cnt, w + i * cnt, b, -half, true, t1, t2))) return rc;
+        }
+    }
+    // z = (rho M)^{-1} w
+    ADS_CK(cudaMemcpyAsync(z, w, b3, cudaMemcpyDeviceToDevice, s->stream));
+    for (int i = 0; i < 3; ++i)
+        if ((rc = kron_solve64(s, z + i * cnt, SET_MASS))) return rc;
+    double wz = 0, vuv = 0, aua = 0;
+    if ((rc = dot3(w, z, &wz))) return rc;
+    wz /= s->rho;
+    if ((rc = apply_upsilon<double>(s, v, z, t1, t2)) || (rc = dot3(v, z, &vuv))) return rc;
+    // average (U^n + U^{n-1})/2 = u - tau/2 v
+    ADS_CK(ads::launch_lincomb<double>(w, 1.0, u, -0.5 * s->tau, v, 3 * cnt, s->stream));
+    if ((rc = apply_upsilon<double>(s, w, z, t1, t2)) || (rc = dot3(w, z, &aua))) return rc;
+    *kin_mod = wz - 0.25 * s->tau * s->tau * vuv + aua;
+    return ADS_OK;
+}
 
 // ====================================================================== ABI
 
@@ -632,8 +864,9 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     if (!(tau > 0.0) || !std::isfinite(tau)) return fail(ADS_ERR_INVALID_ARG, "ads_create: tau must be > 0");
     if (mat->kind != ADS_SCALAR_WAVE && mat->kind != ADS_ELASTIC)
         return fail(ADS_ERR_INVALID_ARG, "ads_create: unknown material kind");
-    if (mat->kind == ADS_ELASTIC) return fail(ADS_ERR_UNSUPPORTED, "ads_create: elasticity not built in this library");
     if (mat->kind == ADS_SCALAR_WAVE && !(mat->c2 > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_create: c2 must be > 0");
+    if (mat->kind == ADS_ELASTIC && !(mat->mu > 0.0 && mat->rho > 0.0 && mat->lambda >= 0.0))
+        return fail(ADS_ERR_INVALID_ARG, "ads_create: elasticity needs mu > 0, rho > 0, lambda >= 0");
     for (int a = 0; a < 3; ++a) {
         if (grid->n_elem[a] < 1) return fail(ADS_ERR_INVALID_ARG, "ads_create: n_elem must be >= 1");
         if (!(grid->length[a] > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_create: length must be > 0");
@@ -653,7 +886,7 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     s->prec = o.precision;
     s->p = p;
     s->tau = tau;
-    s->c2 = mat->c2;
+    s->c2 = mat->kind == ADS_ELASTIC ? 1.0 : mat->c2;
     s->lam = mat->lambda;
     s->mu = mat->mu;
     s->rho = mat->rho;
@@ -707,20 +940,43 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
         return fail(rc, msg);
     }
     const size_t n = (size_t)s->d.count() * elem(s);
-    s->P = dalloc(s, n);
-    s->Q = dalloc(s, n);
-    s->A = dalloc(s, n);
-    s->X = dalloc(s, n);
     s->d_step = (long long *)dalloc(s, sizeof(long long));
     s->d_err = (int *)dalloc(s, sizeof(int));
-    if (!s->P || !s->Q || !s->A || !s->X || !s->d_step || !s->d_err) {
+    bool ok = s->d_step && s->d_err;
+    if (s->kind == ADS_SCALAR_WAVE) {
+        s->P = dalloc(s, n);
+        s->Q = dalloc(s, n);
+        s->A = dalloc(s, n);
+        s->X = dalloc(s, n);
+        ok = ok && s->P && s->Q && s->A && s->X;
+    } else {
+        s->U = dalloc(s, 3 * n);
+        s->Up = dalloc(s, 3 * n);
+        s->R = dalloc(s, 3 * n);
+        s->Y = dalloc(s, 3 * n);
+        s->T1 = dalloc(s, n);
+        s->T2 = dalloc(s, n);
+        ok = ok && s->U && s->Up && s->R && s->Y && s->T1 && s->T2;
+        // bands of M + d K for the discrete invariant (FP64)
+        for (int a = 0; a < 3 && ok; ++a)
+            for (int k = 0; k < 2 && ok; ++k) {
+                const ads::Axis1D &ax = s->ax[a];
+                const double c = k == 0 ? 2 * s->mu + s->lam : s->mu;
+                const double dd = s->tau * s->tau * c / (4 * s->rho);
+                std::vector<double> g(ax.M.v.size());
+                for (size_t i = 0; i < g.size(); ++i) g[i] = ax.M.v[i] + dd * ax.K.v[i];
+                ok = upload<double>(s, pad_rows(g, ax.m, 2 * ax.p + 1, padded(s, ax.m), false), &s->ebandFP64[a][k]) ==
+                     ADS_OK;
+            }
+    }
+    if (!ok) {
         ads_destroy(s);
         return fail(ADS_ERR_OOM, "ads_create: device allocation of the state failed");
     }
-    cudaMemsetAsync(s->P, 0, n, s->stream);
-    cudaMemsetAsync(s->Q, 0, n, s->stream);
-    cudaMemsetAsync(s->A, 0, n, s->stream);
-    cudaMemsetAsync(s->X, 0, n, s->stream);
+    for (void *q : {s->P, s->Q, s->A, s->X, s->U, s->Up, s->R, s->Y})
+        if (q) cudaMemsetAsync(q, 0, q == s->U || q == s->Up || q == s->R || q == s->Y ? 3 * n : n, s->stream);
+    for (void *q : {s->T1, s->T2})
+        if (q) cudaMemsetAsync(q, 0, n, s->stream);
     cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->stream);
     cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
@@ -790,18 +1046,29 @@ int ads_set_state(ads_sim_t *s, const double *u, const double *v, const double *
     if (!s || !u || !v) return fail(ADS_ERR_INVALID_ARG, "ads_set_state: null argument");
     if (count != full_count(s)) return fail(ADS_ERR_INVALID_ARG, "ads_set_state: count does not match the space");
     if (mem != ADS_HOST && mem != ADS_DEVICE) return fail(ADS_ERR_INVALID_ARG, "ads_set_state: mem");
+    if (s->kind == ADS_ELASTIC && a) return fail(ADS_ERR_INVALID_ARG, "ads_set_state: elasticity takes u and v only");
     cudaSetDevice(s->device);
     Scratch sc(s);
+    const int comps = s->kind == ADS_ELASTIC ? 3 : 1;
+    const size_t ncomp = count / comps;
     const size_t ni = (size_t)s->d.count() * sizeof(double);
-    double *tu = (double *)sc.get(ni), *tv = (double *)sc.get(ni), *ta = (double *)sc.get(ni);
+    double *tu = (double *)sc.get(comps * ni), *tv = (double *)sc.get(comps * ni), *ta = (double *)sc.get(ni);
     if (!tu || !tv || !ta) return fail(ADS_ERR_OOM, "ads_set_state: scratch allocation failed");
     int rc;
-    if ((rc = stage_in(s, sc, u, mem, count, tu, 1.0))) return rc;
-    if ((rc = stage_in(s, sc, v, mem, count, tv, 1.0))) return rc;
+    for (int c = 0; c < comps; ++c) {
+        const size_t io = (size_t)c * s->d.count();
+        if ((rc = stage_in(s, sc, u + c * ncomp, mem, ncomp, tu + io, 1.0))) return rc;
+        if ((rc = stage_in(s, sc, v + c * ncomp, mem, ncomp, tv + io, 1.0))) return rc;
+    }
+    ADS_CK(cudaMemcpyAsync(s->d_step, &s->h_step, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+    if (s->kind == ADS_ELASTIC) {
+        if ((rc = elastic_set64(s, sc, tu, tv))) return rc;
+        ADS_CK(cudaStreamSynchronize(s->stream));
+        return ADS_OK;
+    }
     if (a) {
         if ((rc = stage_in(s, sc, a, mem, count, ta, 1.0))) return rc;
     } else {
-        ADS_CK(cudaMemcpyAsync(s->d_step, &s->h_step, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
         if ((rc = consistent_accel64(s, tu, ta))) return rc;
     }
     rc = s->prec == ADS_FP64 ? set_pq<double>(s, tu, tv, ta) : set_pq<float>(s, tu, tv, ta);
@@ -815,16 +1082,16 @@ int ads_set_gaussian_state(ads_sim_t *s, const ads_gaussian_t *u0, const ads_gau
     if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_set_gaussian_state: null sim");
     cudaSetDevice(s->device);
     Scratch sc(s);
-    const size_t ni = (size_t)s->d.count() * sizeof(double);
-    double *tu = (double *)sc.get(ni), *tv = (double *)sc.get(ni), *ta = (double *)sc.get(ni);
+    const int comps = s->kind == ADS_ELASTIC ? 3 : 1;
+    const long long cnt = s->d.count();
+    const size_t ni = (size_t)cnt * sizeof(double);
+    double *tu = (double *)sc.get(comps * ni), *tv = (double *)sc.get(comps * ni), *ta = (double *)sc.get(ni);
     if (!tu || !tv || !ta) return fail(ADS_ERR_OOM, "ads_set_gaussian_state: scratch allocation failed");
     const ads_gaussian_t *gs[2] = {u0, v0};
     double *dst[2] = {tu, tv};
     for (int f = 0; f < 2; ++f) {
-        if (!gs[f]) {
-            ADS_CK(cudaMemsetAsync(dst[f], 0, ni, s->stream));
-            continue;
-        }
+        ADS_CK(cudaMemsetAsync(dst[f], 0, comps * ni, s->stream));
+        if (!gs[f]) continue;
         if (!(gs[f]->den > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_set_gaussian_state: den must be > 0");
         // separable: projection = (Mx^-1 gx) (x) (My^-1 gy) (x) (Mz^-1 gz), done
         // on the device as the outer product of the loads and a mass solve
@@ -836,15 +1103,25 @@ int ads_set_gaussian_state(ads_sim_t *s, const ads_gaussian_t *u0, const ads_gau
             ADS_CK(cudaMemcpyAsync(g[a], h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream));
             ADS_CK(cudaStreamSynchronize(s->stream));
         }
-        ADS_CK(ads::launch_outer((const double *)g[0], (const double *)g[1], (const double *)g[2], gs[f]->amp,
-                                 dst[f], s->d, s->stream));
-        int rc = kron_solve64(s, dst[f], SET_MASS);
-        if (rc) return rc;
+        for (int c = 0; c < comps; ++c) {
+            const double amp = gs[f]->amp * (comps == 3 ? gs[f]->dir[c] : 1.0);
+            if (amp == 0.0) continue;
+            double *dc = dst[f] + (size_t)c * cnt;
+            ADS_CK(ads::launch_outer((const double *)g[0], (const double *)g[1], (const double *)g[2], amp, dc, s->d,
+                                     s->stream));
+            int rc = kron_solve64(s, dc, SET_MASS);
+            if (rc) return rc;
+        }
     }
     s->h_step = 0;
     ADS_CK(cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->stream));
-    int rc = consistent_accel64(s, tu, ta);
-    if (rc) return rc;
+    int rc;
+    if (s->kind == ADS_ELASTIC) {
+        if ((rc = elastic_set64(s, sc, tu, tv))) return rc;
+        ADS_CK(cudaStreamSynchronize(s->stream));
+        return ADS_OK;
+    }
+    if ((rc = consistent_accel64(s, tu, ta))) return rc;
     rc = s->prec == ADS_FP64 ? set_pq<double>(s, tu, tv, ta) : set_pq<float>(s, tu, tv, ta);
     if (rc) return rc;
     ADS_CK(cudaStreamSynchronize(s->stream));
@@ -856,17 +1133,34 @@ int ads_get_state(ads_sim_t *s, double *u, double *v, double *a, size_t count, i
     if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_get_state: null sim");
     if (count != full_count(s)) return fail(ADS_ERR_INVALID_ARG, "ads_get_state: count does not match the space");
     if (mem != ADS_HOST && mem != ADS_DEVICE) return fail(ADS_ERR_INVALID_ARG, "ads_get_state: mem");
+    if (s->kind == ADS_ELASTIC && a) return fail(ADS_ERR_INVALID_ARG, "ads_get_state: elasticity returns u and v only");
     cudaSetDevice(s->device);
     Scratch sc(s);
-    const size_t ni = (size_t)s->d.count() * sizeof(double);
-    double *tu = (double *)sc.get(ni), *tv = (double *)sc.get(ni), *ta = (double *)sc.get(ni);
+    const int comps = s->kind == ADS_ELASTIC ? 3 : 1;
+    const long long cnt = s->d.count();
+    const size_t ni = (size_t)cnt * sizeof(double);
+    double *tu = (double *)sc.get(comps * ni), *tv = (double *)sc.get(comps * ni), *ta = (double *)sc.get(ni);
     if (!tu || !tv || !ta) return fail(ADS_ERR_OOM, "ads_get_state: scratch allocation failed");
-    int rc = s->prec == ADS_FP64 ? get_uva<double>(s, tu, tv, ta) : get_uva<float>(s, tu, tv, ta);
-    if (rc) return rc;
+    int rc;
+    if (s->kind == ADS_ELASTIC) {
+        if (s->prec == ADS_FP64)
+            ADS_CK(ads::launch_el_to_uv<double>((const double *)s->U, (const double *)s->Up, tu, tv, 3 * cnt, s->tau,
+                                                s->stream));
+        else
+            ADS_CK(ads::launch_el_to_uv<float>((const float *)s->U, (const float *)s->Up, tu, tv, 3 * cnt, s->tau,
+                                               s->stream));
+    } else {
+        rc = s->prec == ADS_FP64 ? get_uva<double>(s, tu, tv, ta) : get_uva<float>(s, tu, tv, ta);
+        if (rc) return rc;
+    }
+    const size_t ncomp = count / comps;
     double *outs[3] = {u, v, a};
     double *ins[3] = {tu, tv, ta};
-    for (int f = 0; f < 3; ++f)
-        if (outs[f] && (rc = stage_out(s, sc, ins[f], outs[f], mem, count))) return rc;
+    for (int f = 0; f < 3; ++f) {
+        if (!outs[f]) continue;
+        for (int c = 0; c < comps; ++c)
+            if ((rc = stage_out(s, sc, ins[f] + (size_t)c * cnt, outs[f] + c * ncomp, mem, ncomp))) return rc;
+    }
     return check_device_error(s);
 }
 
@@ -891,7 +1185,7 @@ int ads_step(ads_sim_t *s, int nsteps)
         if ((rc = get_graph(s, chunk, &ge))) return rc;
         const int full = nsteps / chunk;
         for (int i = 0; i < full; ++i) ADS_CK(cudaGraphLaunch(ge, s->stream));
-        ads::g_launches += (unsigned long long)full * chunk * launches_per_step(s);
+        ads::g_launches += (unsigned long long)full * s->graph_launches[chunk];
         nsteps -= full * chunk;
         s->h_step += (long long)full * chunk;
     }
@@ -899,7 +1193,7 @@ int ads_step(ads_sim_t *s, int nsteps)
         cudaGraphExec_t ge;
         if ((rc = get_graph(s, nsteps, &ge))) return rc;
         ADS_CK(cudaGraphLaunch(ge, s->stream));
-        ads::g_launches += (unsigned long long)nsteps * launches_per_step(s);
+        ads::g_launches += s->graph_launches[nsteps];
         s->h_step += nsteps;
     }
     return ADS_OK;
@@ -934,6 +1228,7 @@ int ads_energy(ads_sim_t *s, double *kinetic, double *potential, double *kin_mod
 {
     if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_energy: null sim");
     cudaSetDevice(s->device);
+    if (s->kind == ADS_ELASTIC) return elastic_energy(s, kinetic, potential, kin_mod);
     Scratch sc(s);
     const size_t ni = (size_t)s->d.count() * sizeof(double);
     double *u = (double *)sc.get(ni), *v = (double *)sc.get(ni), *w = (double *)sc.get(ni), *t = (double *)sc.get(ni);
@@ -979,23 +1274,47 @@ int ads_apply(ads_sim_t *s, int op, const double *in, double *out, size_t count,
     return stage_out(s, sc, y, out, mem, count);
 }
 
+// raw state arrays of the simulation: scalar wave p, q, a; elasticity U^n, U^{n-1}
+static int state_arrays(ads_sim_t *s, void **arr, size_t *bytes)
+{
+    const size_t n = (size_t)s->d.count() * elem(s);
+    if (s->kind == ADS_ELASTIC) {
+        arr[0] = s->U;
+        arr[1] = s->Up;
+        bytes[0] = bytes[1] = 3 * n;
+        return 2;
+    }
+    arr[0] = s->P;
+    arr[1] = s->Q;
+    arr[2] = s->A;
+    bytes[0] = bytes[1] = bytes[2] = n;
+    return 3;
+}
+
 size_t ads_checkpoint_bytes(const ads_sim_t *s)
 {
     if (!s) return 0;
-    return 3 * (size_t)s->d.count() * elem(s) + sizeof(long long);
+    void *arr[3];
+    size_t b[3], tot = sizeof(long long);
+    const int k = state_arrays(const_cast<ads_sim_t *>(s), arr, b);
+    for (int i = 0; i < k; ++i) tot += b[i];
+    return tot;
 }
 
 int ads_checkpoint_save(ads_sim_t *s, void *host, size_t bytes)
 {
     if (!s || !host || bytes != ads_checkpoint_bytes(s)) return fail(ADS_ERR_INVALID_ARG, "ads_checkpoint_save: bad arguments");
     cudaSetDevice(s->device);
-    const size_t n = (size_t)s->d.count() * elem(s);
+    void *arr[3];
+    size_t b[3];
+    const int k = state_arrays(s, arr, b);
     char *h = (char *)host;
-    ADS_CK(cudaMemcpyAsync(h, s->P, n, cudaMemcpyDeviceToHost, s->stream));
-    ADS_CK(cudaMemcpyAsync(h + n, s->Q, n, cudaMemcpyDeviceToHost, s->stream));
-    ADS_CK(cudaMemcpyAsync(h + 2 * n, s->A, n, cudaMemcpyDeviceToHost, s->stream));
+    for (int i = 0; i < k; ++i) {
+        ADS_CK(cudaMemcpyAsync(h, arr[i], b[i], cudaMemcpyDeviceToHost, s->stream));
+        h += b[i];
+    }
     ADS_CK(cudaStreamSynchronize(s->stream));
-    std::memcpy(h + 3 * n, &s->h_step, sizeof(long long));
+    std::memcpy(h, &s->h_step, sizeof(long long));
     return ADS_OK;
 }
 
@@ -1003,12 +1322,15 @@ int ads_checkpoint_load(ads_sim_t *s, const void *host, size_t bytes)
 {
     if (!s || !host || bytes != ads_checkpoint_bytes(s)) return fail(ADS_ERR_INVALID_ARG, "ads_checkpoint_load: bad arguments");
     cudaSetDevice(s->device);
-    const size_t n = (size_t)s->d.count() * elem(s);
+    void *arr[3];
+    size_t b[3];
+    const int k = state_arrays(s, arr, b);
     const char *h = (const char *)host;
-    ADS_CK(cudaMemcpyAsync(s->P, h, n, cudaMemcpyHostToDevice, s->stream));
-    ADS_CK(cudaMemcpyAsync(s->Q, h + n, n, cudaMemcpyHostToDevice, s->stream));
-    ADS_CK(cudaMemcpyAsync(s->A, h + 2 * n, n, cudaMemcpyHostToDevice, s->stream));
-    std::memcpy(&s->h_step, h + 3 * n, sizeof(long long));
+    for (int i = 0; i < k; ++i) {
+        ADS_CK(cudaMemcpyAsync(arr[i], h, b[i], cudaMemcpyHostToDevice, s->stream));
+        h += b[i];
+    }
+    std::memcpy(&s->h_step, h, sizeof(long long));
     ADS_CK(cudaMemcpyAsync(s->d_step, &s->h_step, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
     ADS_CK(cudaStreamSynchronize(s->stream));
     return ADS_OK;
@@ -1065,7 +1387,11 @@ int ads_profile_step(ads_sim_t *s, const char **names, float *ms, int cap, int *
     if (!s || !count || cap < 0) return fail(ADS_ERR_INVALID_ARG, "ads_profile_step: bad arguments");
     cudaSetDevice(s->device);
     KernelTimer kt;
-    int rc = s->prec == ADS_FP64 ? pwave_step<double>(s, true, &kt) : pwave_step<float>(s, true, &kt);
+    int rc;
+    if (s->kind == ADS_ELASTIC)
+        rc = s->prec == ADS_FP64 ? elastic_step<double>(s, &kt) : elastic_step<float>(s, &kt);
+    else
+        rc = s->prec == ADS_FP64 ? pwave_step<double>(s, true, &kt) : pwave_step<float>(s, true, &kt);
     if (rc) return rc;
     s->h_step += 1;
     s->warmed = true;

@@ -680,7 +680,10 @@ __global__ void k_axis_apply(const T *__restrict__ band, int axis, const T *__re
         const long long rem = idx - (long long)z * plane;
         const int y = (int)(rem / d.sx);
         const int x = (int)(rem - (long long)y * d.sx);
-        if (x >= d.mx) continue;
+        if (x >= d.mx) {   // row padding stays zero, so dot products may span it
+            out[idx] = T(0);
+            continue;
+        }
         int i, m;
         long long st;
         if (axis == 0) { i = x; m = d.mx; st = 1; }
@@ -869,6 +872,54 @@ __global__ void k_dot_final(const double *partial, int nb, double *result)
         c += partial[2 * b + 1];
     }
     result[0] = s + c;
+}
+
+template <typename T>
+__global__ void k_lincomb(T *out, T a, const T *x, T b, const T *y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + (y ? b * y[i] : T(0));
+}
+
+template <typename T>
+__global__ void k_atm_update(T *U, T *Up, const T *d, long long n, long long *step)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && step) step[0] += 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T u = U[i];
+        U[i] = T(2) * u - Up[i] + d[i];
+        Up[i] = u;
+    }
+}
+
+template <typename T>
+__global__ void k_add_source(T *out, Dims d, const T *fx, const T *fy, const T *fz, double scale, double freq,
+                             double t0, const long long *step, int toff, double tau)
+{
+    __shared__ T s_c;
+    if (threadIdx.x == 0) s_c = (T)(scale * ricker_dev(freq, t0, (double)(step[0] + toff) * tau));
+    __syncthreads();
+    const T c = s_c;
+    const long long n = d.count();
+    const long long plane = d.plane();
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int z = (int)(idx / plane);
+        const long long rem = idx - (long long)z * plane;
+        const int y = (int)(rem / d.sx);
+        const int x = (int)(rem - (long long)y * d.sx);
+        if (x < d.mx) out[idx] += c * fz[z] * fy[y] * fx[x];
+    }
+}
+
+template <typename T>
+__global__ void k_el_to_uv(const T *U, const T *Up, double *u, double *v, long long n, double tau)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double a = (double)U[i], b = (double)Up[i];
+        if (u) u[i] = a;
+        if (v) v[i] = (a - b) / tau;
+    }
 }
 
 inline int grid_for(long long n, int bs)
@@ -1117,6 +1168,39 @@ cudaError_t launch_dot(const double *x, const double *y, long long n, double *pa
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_lincomb(T *out, T a, const T *x, T b, const T *y, long long n, cudaStream_t s)
+{
+    ++g_launches;
+    k_lincomb<T><<<grid_for(n, 256), 256, 0, s>>>(out, a, x, b, y, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_atm_update(T *U, T *Up, const T *d, long long n, long long *step, cudaStream_t s)
+{
+    ++g_launches;
+    k_atm_update<T><<<grid_for(n, 256), 256, 0, s>>>(U, Up, d, n, step);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_add_source(T *out, Dims d, const T *fx, const T *fy, const T *fz, double scale, double freq,
+                              double t0, const long long *step, int toff, double tau, cudaStream_t s)
+{
+    ++g_launches;
+    k_add_source<T><<<grid_for(d.count(), 256), 256, 0, s>>>(out, d, fx, fy, fz, scale, freq, t0, step, toff, tau);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long long n, double tau, cudaStream_t s)
+{
+    ++g_launches;
+    k_el_to_uv<T><<<grid_for(n, 256), 256, 0, s>>>(U, Up, u, v, n, tau);
+    return cudaGetLastError();
+}
+
 #define ADS_INST(T)                                                                                                \
     template cudaError_t launch_rhs<T>(int, int, const RhsArgs<T> &, cudaStream_t);                                \
     template cudaError_t launch_col<T>(int, int, const ColArgs<T> &, cudaStream_t);                                \
@@ -1129,7 +1213,12 @@ cudaError_t launch_dot(const double *x, const double *y, long long n, double *pa
     template cudaError_t launch_pq_to_uva<T>(const T *, const T *, const T *, double *, double *, double *, Dims,  \
                                              double, cudaStream_t);                                                \
     template cudaError_t launch_convert<T>(const T *, double *, long long, cudaStream_t);                          \
-    template cudaError_t launch_convert_from<T>(const double *, T *, long long, cudaStream_t);
+    template cudaError_t launch_convert_from<T>(const double *, T *, long long, cudaStream_t);                      \
+    template cudaError_t launch_lincomb<T>(T *, T, const T *, T, const T *, long long, cudaStream_t);              \
+    template cudaError_t launch_atm_update<T>(T *, T *, const T *, long long, long long *, cudaStream_t);          \
+    template cudaError_t launch_add_source<T>(T *, Dims, const T *, const T *, const T *, double, double, double,   \
+                                              const long long *, int, double, cudaStream_t);                       \
+    template cudaError_t launch_el_to_uv<T>(const T *, const T *, double *, double *, long long, double, cudaStream_t);
 
 ADS_INST(float)
 ADS_INST(double)

@@ -135,6 +135,20 @@ cudaError_t launch_convert_from(const double *x, T *y, long long n, cudaStream_t
 cudaError_t launch_dot(const double *x, const double *y, long long n, double *partial, int nblocks,
                        double *result, cudaStream_t s);
 
+// out = a*x + b*y over n elements (y may be null)
+template <typename T>
+cudaError_t launch_lincomb(T *out, T a, const T *x, T b, const T *y, long long n, cudaStream_t s);
+// three-level update (elasticity): t = U; U = 2U - Up + d; Up = t; step[0] += 1
+template <typename T>
+cudaError_t launch_atm_update(T *U, T *Up, const T *d, long long n, long long *step, cudaStream_t s);
+// out[z][y][x] += scale * ricker(t) * fz[z] fy[y] fx[x],  t = (step[0] + toff) * tau
+template <typename T>
+cudaError_t launch_add_source(T *out, Dims d, const T *fx, const T *fy, const T *fz, double scale, double freq,
+                              double t0, const long long *step, int toff, double tau, cudaStream_t s);
+// FP64 views of the elastic state: u = U, v = (U - Up)/tau
+template <typename T>
+cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long long n, double tau, cudaStream_t s);
+
 extern unsigned long long g_launches;
 
 }  // namespace ads

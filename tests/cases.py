@@ -79,3 +79,39 @@ def check_state(got, ref, precision, tau, base, what=""):
     tv, ta = derived_tols(ref[0], ref[1], ref[2], tau, base)
     assert_parity(got[1], ref[1], tv, what + " v (tol %.1e)" % tv)
     assert_parity(got[2], ref[2], ta, what + " a (tol %.1e)" % ta)
+
+
+def oracle_elastic(case, steps, checkpoints=(), source=None):
+    """Returns {step: (U, V)} with V = (U^n - U^{n-1})/tau (full arrays)."""
+    s = ora.Space(case.n_elem, case.p)
+    V0 = np.zeros((3,) + s.shape)
+    if case.v0:
+        g = s.project_gauss(case.v0["amp"], case.v0["center"], case.v0["den"])
+        V0 = np.stack([case.v0["dir"][i] * g for i in range(3)])
+    U0 = np.zeros_like(V0)
+    kw = {}
+    if source:
+        G = s.load_gauss(source["amp"], source["center"], source["den"])
+        kw = dict(G=G, direction=np.asarray(source["dir"], float), rick=(source["freq"], source["t0"]))
+    Up = s.elastic_start(case.tau, case.lam, case.mu, case.rho, U0, V0, **kw, **({"t0": 0.0} if kw else {}))
+    out, done, U = {}, 0, U0
+    for target in sorted(set(checkpoints) | {steps}):
+        U, Up = s.elastic_run(case.tau, case.lam, case.mu, case.rho, target - done, U, Up, step0=done, **kw)
+        done = target
+        out[target] = (s.pad(U), s.pad((U - Up) / case.tau))
+    return out
+
+
+def gpu_elastic(case, steps, precision="fp64", checkpoints=(), source=None):
+    from paper_1911_08158_gb300 import Simulation
+    sim = Simulation(case.n_elem, case.p, case.tau, kind="elastic", lam=case.lam, mu=case.mu, rho=case.rho,
+                     precision=precision)
+    if source:
+        sim.set_source(source)
+    sim.set_gaussian_state(None, case.v0)
+    out, done = {}, 0
+    for target in sorted(set(checkpoints) | {steps}):
+        sim.step(target - done)
+        done = target
+        out[target] = sim.get_state()[:2]
+    return sim, out
