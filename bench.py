@@ -9,12 +9,20 @@ path (FP32 state and sweeps, FP64 1D factors).  DOF counts include boundary
 coefficients.  The L2 cache is flushed (a 512 MB write) before every timed
 step; inputs stay resident in HBM.
 
-  value  : device time (CUDA events on the simulations' stream), whole job
+  value  : device time (CUDA events on the simulations' stream), whole job;
+           both simulations advance together through ads_batch_step (one
+           grouped launch per kernel and degree, the two degrees overlapping)
   e2e    : the same metric through the C ABI with pinned host buffers: per
            step set_state(u, v, a) from host, 200 steps, get_state to host
   fp64   : the FP64 path on the same workload (the path the FP32 one beats)
   roofline: dominant kernel, algorithmic bytes / its CUDA-event time
   cpu_baseline: the FP64 CPU oracle on a bounded sample of the workload
+  batch  : 64 uneven P-wave simulations (elements per axis U{32..160}, p in
+           {2, 3}, tau in [1e-3, 5e-3], Gaussian pulses), 50 steps each, FP32,
+           autotuned tiles, grouped launches replayed from CUDA graphs
+  serving: 500 Poisson-arrival requests (20/s, 80% P-wave / 20% elasticity,
+           grids log-uniform 24..256 per axis, 10..500 steps) under a 150 GB
+           budget: p50/p99 latency and DOF-steps/s
 
 --impl reference runs the CPU oracle as the reference arm (there is no
 reference implementation of this paper; the oracle is the plain restatement).
@@ -137,11 +145,11 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     sims = make_sims("fp32", torch, ads, wl, stream)
+    tiles = [s.autotune(3) for s in sims]
     dof_steps = sum(dofs(s) for s in sims) * NSTEPS
 
     def bench_step():
-        for s in sims:
-            s.step(NSTEPS)
+        ads.batch_step(sims, NSTEPS)
 
     for _ in range(args.warmup):
         bench_step()
@@ -273,12 +281,16 @@ def run_ours(args):
         "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_elem": NE, "p": list(PS), "tau": 2e-3, "newmark_steps": NSTEPS,
-                   "dofs": [dofs(s) for s in sims], "dof_steps_per_step": dof_steps,
+                   "dofs": [dofs(s) for s in sims], "dof_steps_per_step": dof_steps, "k1_tile_rows": tiles,
                    "l2": "flushed (512 MB write) before each timed step", "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": e2e, "gpu_launches": int(launches), "wall_s": wall,
         "fp64": fp64, "rel_l2_fp32_vs_fp64_u": acc,
         "roofline": roofline, "clocks": clk.summary(),
     }
+    if not args.no_batch:
+        out["batch"] = guarded(run_batch, args, stream, flush)
+    if not args.no_serve:
+        out["serving"] = guarded(run_serving, args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if ws > 1:
@@ -287,6 +299,61 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def guarded(fn, *a):
+    """A secondary measurement must not cost the main line."""
+    try:
+        return fn(*a)
+    except Exception as e:   # noqa: BLE001
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
+def run_batch(args, stream, flush):
+    """64 uneven simulations advanced together (grouped launches + graphs)."""
+    import torch
+
+    import paper_1911_08158_gb300 as ads
+    from paper_1911_08158_gb300 import workloads as wl
+    cases = wl.batch_cases(count=64, seed=0, steps=50)
+    sims = []
+    for c in cases:
+        sim = ads.Simulation(c.n_elem, c.p, c.tau, precision="fp32", stream=stream)
+        sim.set_gaussian_state(c.u0, None)
+        sims.append(sim)
+    tiles = [s.autotune(3) for s in sims]
+    dof_steps = sum(dofs(s) for s in sims) * 50
+    ads.batch_step(sims, 50)   # warm-up: first grouped step, graph capture
+    torch.cuda.synchronize()
+    reps = max(1, min(args.steps, 5))
+    t = 0.0
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ads.batch_step(sims, 50)
+        e1.record(stream)
+        e1.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+    n = sum(dofs(s) for s in sims)
+    for s in sims:
+        s.close()
+    return {"value": dof_steps * reps / t, "unit": UNIT, "simulations": len(cases), "steps_each": 50,
+            "total_dofs": n, "reps": reps, "ms_per_rep": t / reps * 1e3,
+            "tiles_fused": sum(1 for s, r in zip(cases, tiles) if r == s.n_elem[1] + s.p - 2),
+            "workload": "batch64_pwave_uneven_32to160_p2p3_50steps_fp32"}
+
+
+def run_serving(args):
+    from paper_1911_08158_gb300 import workloads as wl
+    from paper_1911_08158_gb300.serve import Server
+    reqs = wl.serving_requests(count=args.serve_requests, rate=20.0, seed=0)
+    rep = Server(150 * 10 ** 9, precision="fp32", chunk=16).run(reqs)
+    out = rep.summary()
+    out.update(workload="serving_poisson20_%dreq_wave80_elastic20_24to256_budget150GB_fp32" % len(reqs),
+               unit_latency="s")
+    return out
 
 
 def oracle_sample(seconds: float, p: int = 2):
@@ -369,6 +436,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-simulation batch measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=500)
     ap.add_argument("--profile-case", default="", help="run a small case (n or nx,ny,nz elements) for ncu and exit")
     ap.add_argument("--profile-p", type=int, default=2)
     args = ap.parse_args()

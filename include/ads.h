@@ -158,9 +158,29 @@ int ads_get_state(ads_sim_t *sim, double *u, double *v, double *a, size_t count,
 /* Advance nsteps >= 0 time steps (asynchronous on the stream). */
 int ads_step(ads_sim_t *sim, int nsteps);
 
-/* Advance several simulations (same device) by nsteps each in one launch
- * sequence; simulations of equal shape and precision share launches. */
+/* Advance `count` distinct simulations (same device) by nsteps each.
+ * Scalar-wave simulations of equal precision and degree, whatever their
+ * grids, tiles and sources, advance together: each time step is one grouped
+ * launch of K1 over all their z-planes (up to 32 simulations per launch),
+ * one of the y sweep for those whose K1 tile does not span y, and one of the
+ * z sweep + update; runs of 16 steps replay a captured CUDA graph (cached
+ * per member set).  Each (precision, degree) group runs on a stream of its
+ * own, ordered after the members' streams and before their later work, so
+ * groups overlap on the device.  Elasticity simulations step on their own
+ * streams.  Every result equals what ads_step gives the simulation alone
+ * (the members share no data).  Errors: INVALID_ARG (null or repeated
+ * simulation, mixed devices, nsteps < 0), CUDA. */
 int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps);
+
+/* Autotuner of the K1 line tile: times every tile height K1 can take for
+ * this grid (whole z-plane with the fused y sweep when it fits shared
+ * memory; 8, 16, 32 or 64 rows with a separate y sweep) for trial_steps
+ * steps each on the simulation itself, restores its state and step counter
+ * after every trial, and keeps the fastest.  The choice is cached for the
+ * process per (grid, p, precision, kind): later calls for the same shape
+ * apply it without timing.  trial_steps = 0 takes the default tile.
+ * *tile_rows (nullable) receives the chosen height.  Waits. */
+int ads_autotune(ads_sim_t *sim, int trial_steps, int *tile_rows);
 
 /* Wait for the simulation's stream; reports asynchronous CUDA errors. */
 int ads_sync(ads_sim_t *sim);
@@ -207,6 +227,13 @@ int ads_checkpoint_load(ads_sim_t *sim, const void *host_buf, size_t bytes);
 
 /* Device bytes held by the simulation (state, scratch, factors). */
 size_t ads_device_bytes(const ads_sim_t *sim);
+
+/* Upper bound of the device bytes a simulation of this shape holds once
+ * created with a source set (state and tables, each allocation rounded up as
+ * a caching allocator rounds it), for admission control before creating it.
+ * kind: ADS_SCALAR_WAVE | ADS_ELASTIC; precision: ADS_FP64 | ADS_FP32.
+ * Returns 0 for invalid arguments.  Host only, no device access. */
+size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision);
 
 /* Measurement: run ONE time step with CUDA events recorded on the
  * simulation's stream between its kernels; fills names[i] (static strings)

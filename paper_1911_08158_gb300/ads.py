@@ -84,6 +84,9 @@ def library() -> ctypes.CDLL:
         L.ads_get_state.argtypes = [vp, vp, vp, vp, sz, i]
         L.ads_step.argtypes = [vp, i]
         L.ads_batch_step.argtypes = [ctypes.POINTER(vp), i, i]
+        L.ads_autotune.argtypes = [vp, i, ctypes.POINTER(i)]
+        L.ads_estimate_bytes.argtypes = [ctypes.POINTER(Grid), i, i, i]
+        L.ads_estimate_bytes.restype = sz
         L.ads_sync.argtypes = [vp]
         L.ads_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.ads_energy.argtypes = [vp, _D, _D, _D]
@@ -333,7 +336,25 @@ class Simulation:
     def device_bytes(self) -> int:
         return int(library().ads_device_bytes(self._h))
 
+    def autotune(self, trial_steps: int = 3) -> int:
+        """Pick the K1 tile height by timing the candidates (ads_autotune); returns it."""
+        rows = ctypes.c_int(0)
+        _check(library().ads_autotune(self._h, int(trial_steps), ctypes.byref(rows)))
+        return rows.value
+
+
+def estimate_bytes(n_elem, p: int, kind: str = "wave", precision: str = "fp32") -> int:
+    """Device bytes a simulation of this shape will hold (ads_estimate_bytes)."""
+    ne = tuple(int(v) for v in (n_elem if np.ndim(n_elem) else (n_elem,) * 3))
+    g = Grid((ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(1.0, 1.0, 1.0))
+    k = {"wave": ADS_SCALAR_WAVE, "elastic": ADS_ELASTIC}[kind]
+    prec = {"fp64": ADS_FP64, "fp32": ADS_FP32}[precision]
+    return int(library().ads_estimate_bytes(ctypes.byref(g), int(p), k, prec))
+
 
 def batch_step(sims, nsteps: int):
+    """Advance all simulations by nsteps with grouped launches (ads_batch_step)."""
+    if not sims:
+        return
     arr = (ctypes.c_void_p * len(sims))(*[s.handle.value for s in sims])
     _check(library().ads_batch_step(arr, len(sims), int(nsteps)))

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -94,6 +95,11 @@ struct ads_sim {
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, unsigned long long> graph_launches;
     bool warmed = false;
+    // identity for cached batch graphs: uid is unique per process, version
+    // changes whenever the launch arguments change (tables, tiles)
+    unsigned long long uid = 0, version = 0;
+    ads::ColMaps upd_maps{};   // TMA maps of P, Q for the z epilogue (scalar wave)
+    bool has_maps = false;
 };
 
 namespace {
@@ -532,28 +538,31 @@ struct KernelTimer {
     }
 };
 
-// One scalar-wave step: K1 (RHS + x [+ y]), K2 (y) if needed, K3 (z + update).
+// Launch arguments of one scalar-wave step: K1 (RHS + x [+ y]), K2 (y
+// sweep, only when K1's tile does not span y), K3 (z sweep + update).
 template <typename T>
-int pwave_step(ads_sim *s, bool write_a, KernelTimer *kt = nullptr)
+struct PwaveLaunch {
+    ads::RhsArgs<T> rhs;
+    ads::ColArgs<T> ycol, zcol;
+    bool fused;
+};
+
+template <typename T>
+PwaveLaunch<T> pwave_launch(const ads_sim *s, bool write_a)
 {
     const TableSet &ts = tables_for<T>(s);
-    ads::RhsArgs<T> r = rhs_args<T>(s, (const T *)s->P, (T *)s->X, SET_SPLIT, 1, true);
-    const bool fused = r.ty == s->d.my;
-    int rc;
-    if (kt && (rc = kt->mark(s->stream, fused ? "rhs_xy_sweep" : "rhs_x_sweep"))) return rc;
-    ADS_CK(ads::launch_rhs<T>(s->p, s->seg, r, s->stream));
+    PwaveLaunch<T> L;
+    L.rhs = rhs_args<T>(s, (const T *)s->P, (T *)s->X, SET_SPLIT, 1, true);
+    L.fused = L.rhs.ty == s->d.my;
     ads::ColArgs<T> c{};
     c.d = s->d;
     c.in = (const T *)s->X;
     c.out = (T *)s->X;
     c.err = s->d_err;
-    if (!fused) {
-        c.axis = 1;
-        c.mode = 0;
-        c.ln = line_dev<T>(ts.line[SET_SPLIT][1]);
-        if (kt && (rc = kt->mark(s->stream, "y_sweep"))) return rc;
-        ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
-    }
+    c.axis = 1;
+    c.mode = 0;
+    c.ln = line_dev<T>(ts.line[SET_SPLIT][1]);
+    L.ycol = c;
     c.axis = 2;
     c.mode = 1;
     c.ln = line_dev<T>(ts.line[SET_SPLIT][2]);
@@ -563,9 +572,52 @@ int pwave_step(ads_sim *s, bool write_a, KernelTimer *kt = nullptr)
     c.tau2 = (T)(s->tau * s->tau);
     c.write_a = write_a ? 1 : 0;
     c.step = s->d_step;
+    L.zcol = c;
+    return L;
+}
+
+// One scalar-wave step of one simulation (a group of one).
+template <typename T>
+int pwave_step(ads_sim *s, bool write_a, KernelTimer *kt = nullptr)
+{
+    const PwaveLaunch<T> L = pwave_launch<T>(s, write_a);
+    int rc;
+    if (kt && (rc = kt->mark(s->stream, L.fused ? "rhs_xy_sweep" : "rhs_x_sweep"))) return rc;
+    ADS_CK(ads::launch_rhs_group<T>(s->p, &L.rhs, 1, s->stream));
+    if (!L.fused) {
+        if (kt && (rc = kt->mark(s->stream, "y_sweep"))) return rc;
+        ADS_CK(ads::launch_col_group<T>(s->p, &L.ycol, nullptr, 1, s->stream));
+    }
     if (kt && (rc = kt->mark(s->stream, "z_sweep_update"))) return rc;
-    ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    ADS_CK(ads::launch_col_group<T>(s->p, &L.zcol, s->has_maps ? &s->upd_maps : nullptr, 1, s->stream));
     if (kt && (rc = kt->mark(s->stream, ""))) return rc;
+    return ADS_OK;
+}
+
+// One scalar-wave step of a group of simulations of one degree and
+// precision, in three grouped launches on stream st (Sec. 2 step for every
+// member; the members are independent, so each result is the one its
+// simulation gets alone).
+template <typename T>
+int pwave_group_step(const std::vector<ads_sim *> &g, cudaStream_t st, bool write_a)
+{
+    if (g.empty()) return ADS_OK;
+    std::vector<ads::RhsArgs<T>> r;
+    std::vector<ads::ColArgs<T>> ya, za;
+    std::vector<ads::ColMaps> zm;
+    bool all_maps = true;
+    for (ads_sim *s : g) {
+        const PwaveLaunch<T> L = pwave_launch<T>(s, write_a);
+        r.push_back(L.rhs);
+        if (!L.fused) ya.push_back(L.ycol);
+        za.push_back(L.zcol);
+        zm.push_back(s->upd_maps);
+        all_maps = all_maps && s->has_maps;
+    }
+    const int p = g[0]->p;
+    ADS_CK(ads::launch_rhs_group<T>(p, r.data(), (int)r.size(), st));
+    if (!ya.empty()) ADS_CK(ads::launch_col_group<T>(p, ya.data(), nullptr, (int)ya.size(), st));
+    ADS_CK(ads::launch_col_group<T>(p, za.data(), all_maps ? zm.data() : nullptr, (int)za.size(), st));
     return ADS_OK;
 }
 
@@ -772,6 +824,15 @@ int get_graph(ads_sim *s, int chunk, cudaGraphExec_t *out)
     return ADS_OK;
 }
 
+// Captured graphs hold launch arguments: drop them whenever those change.
+void drop_graphs(ads_sim *s)
+{
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    s->graph_launches.clear();
+    ++s->version;
+}
+
 // K1 images carry the source vectors: rebuild after a source change, and
 // drop captured graphs (they hold the old image pointers)
 int rebuild_images(ads_sim *s)
@@ -781,9 +842,284 @@ int rebuild_images(ads_sim *s)
         if (rc) return rc;
         if (s->prec == ADS_FP32 && (rc = upload_rhs_image<float>(s, s->t32, set))) return rc;
     }
-    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
-    s->graphs.clear();
-    s->graph_launches.clear();
+    drop_graphs(s);
+    return ADS_OK;
+}
+
+
+// ------------------------------------------------------------------ batching
+
+// Process-wide resources of grouped launches on one device: one stream per
+// (precision, degree) group so that groups overlap, and a small cache of
+// captured batch graphs keyed by the members' identities.
+struct BatchKey {
+    int prec, p, chunk;
+    std::vector<std::pair<unsigned long long, unsigned long long>> ids;   // (uid, version) per member
+    bool operator<(const BatchKey &o) const
+    {
+        if (prec != o.prec) return prec < o.prec;
+        if (p != o.p) return p < o.p;
+        if (chunk != o.chunk) return chunk < o.chunk;
+        return ids < o.ids;
+    }
+};
+
+struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;
+    unsigned long long last_use = 0;
+};
+
+struct BatchRes {
+    std::map<std::pair<int, int>, cudaStream_t> streams;
+    std::map<BatchKey, BatchGraph> graphs;
+    unsigned long long clock = 0;
+};
+
+constexpr int kBatchChunk = 16;        // steps per captured batch graph
+constexpr size_t kBatchGraphs = 16;    // cached batch graphs per device
+
+BatchRes &batch_res(int device)
+{
+    static std::map<int, BatchRes> res;
+    return res[device];
+}
+
+int group_stream(BatchRes &br, int prec, int p, cudaStream_t *out)
+{
+    auto it = br.streams.find({prec, p});
+    if (it == br.streams.end()) {
+        cudaStream_t st;
+        ADS_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        it = br.streams.emplace(std::make_pair(prec, p), st).first;
+    }
+    *out = it->second;
+    return ADS_OK;
+}
+
+int group_steps(const std::vector<ads_sim *> &g, cudaStream_t st, int n, bool write_last)
+{
+    for (int i = 0; i < n; ++i) {
+        const bool wa = write_last && i == n - 1;
+        int rc = g[0]->prec == ADS_FP64 ? pwave_group_step<double>(g, st, wa) : pwave_group_step<float>(g, st, wa);
+        if (rc) return rc;
+    }
+    return ADS_OK;
+}
+
+// captured graph of kBatchChunk grouped steps for the members of g
+int batch_graph(BatchRes &br, const std::vector<ads_sim *> &g, cudaStream_t st, BatchGraph **out)
+{
+    BatchKey key{g[0]->prec, g[0]->p, kBatchChunk, {}};
+    for (ads_sim *s : g) key.ids.push_back({s->uid, s->version});
+    auto it = br.graphs.find(key);
+    if (it == br.graphs.end()) {
+        if (br.graphs.size() >= kBatchGraphs) {   // evict the least recently used
+            auto lru = br.graphs.begin();
+            for (auto jt = br.graphs.begin(); jt != br.graphs.end(); ++jt)
+                if (jt->second.last_use < lru->second.last_use) lru = jt;
+            cudaGraphExecDestroy(lru->second.exec);
+            br.graphs.erase(lru);
+        }
+        cudaGraph_t graph = nullptr;
+        const unsigned long long before = ads::g_launches;
+        ADS_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = group_steps(g, st, kBatchChunk, true);
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        const unsigned long long launches = ads::g_launches - before;
+        ads::g_launches = before;
+        if (rc != ADS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(ADS_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(ADS_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+        BatchGraph bg;
+        bg.exec = ge;
+        bg.launches = launches;
+        it = br.graphs.emplace(key, bg).first;
+    }
+    it->second.last_use = ++br.clock;
+    *out = &it->second;
+    return ADS_OK;
+}
+
+// Advance every group by nsteps: each group runs on its own stream after
+// the members' streams (pending work on any member) and the members'
+// streams wait for it again, so stream order per simulation is kept.
+int batch_groups(std::map<std::pair<int, int>, std::vector<ads_sim *>> &groups, int nsteps)
+{
+    if (groups.empty()) return ADS_OK;
+    BatchRes &br = batch_res(groups.begin()->second[0]->device);
+    std::vector<cudaEvent_t> evs;
+    auto new_event = [&](cudaEvent_t *e) -> int {
+        ADS_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        evs.push_back(*e);
+        return ADS_OK;
+    };
+    struct Cleanup {
+        std::vector<cudaEvent_t> &e;
+        ~Cleanup()
+        {
+            for (cudaEvent_t x : e) cudaEventDestroy(x);
+        }
+    } cleanup{evs};
+    int rc;
+    for (auto &kv : groups) {
+        std::vector<ads_sim *> &g = kv.second;
+        cudaStream_t st;
+        if ((rc = group_stream(br, kv.first.first, kv.first.second, &st))) return rc;
+        std::vector<cudaStream_t> member_streams;
+        for (ads_sim *s : g)
+            if (std::find(member_streams.begin(), member_streams.end(), s->stream) == member_streams.end())
+                member_streams.push_back(s->stream);
+        for (cudaStream_t ms : member_streams) {
+            cudaEvent_t e;
+            if ((rc = new_event(&e))) return rc;
+            ADS_CK(cudaEventRecord(e, ms));
+            ADS_CK(cudaStreamWaitEvent(st, e, 0));
+        }
+        int left = nsteps;
+        bool warmed = true;
+        for (ads_sim *s : g) warmed = warmed && s->warmed;
+        if (!warmed) {   // first grouped step outside capture (kernel attributes)
+            if ((rc = group_steps(g, st, 1, left == 1))) return rc;
+            for (ads_sim *s : g) s->warmed = true;
+            --left;
+        }
+        if (left >= kBatchChunk) {
+            BatchGraph *bg;
+            if ((rc = batch_graph(br, g, st, &bg))) return rc;
+            const int full = left / kBatchChunk;
+            for (int i = 0; i < full; ++i) ADS_CK(cudaGraphLaunch(bg->exec, st));
+            ads::g_launches += (unsigned long long)full * bg->launches;
+            left -= full * kBatchChunk;
+        }
+        if (left > 0 && (rc = group_steps(g, st, left, true))) return rc;
+        for (ads_sim *s : g) s->h_step += nsteps;
+        cudaEvent_t done;
+        if ((rc = new_event(&done))) return rc;
+        ADS_CK(cudaEventRecord(done, st));
+        for (cudaStream_t ms : member_streams) ADS_CK(cudaStreamWaitEvent(ms, done, 0));
+    }
+    return ADS_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+
+// Tile heights K1 can take for this simulation: the whole plane (fused y
+// sweep) when it fits the shared-memory budget, and row tiles of 8..64
+// rows with a separate y sweep.
+std::vector<int> tile_candidates(const ads_sim *s)
+{
+    const int el = (int)elem(s);
+    const int Sx = segs(s, s->d.mx), Sy = segs(s, s->d.my), my = s->d.my;
+    std::vector<int> c;
+    if (ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy) <= 220 * 1024) c.push_back(my);
+    for (int t : {8, 16, 32, 64})
+        if (t < my && ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy) <= 220 * 1024) c.push_back(t);
+    return c;
+}
+
+struct TuneKey {
+    int mx, my, mz, p, prec, kind;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(mx, my, mz, p, prec, kind) < std::tie(o.mx, o.my, o.mz, o.p, o.prec, o.kind);
+    }
+};
+
+std::map<TuneKey, int> &tune_cache()
+{
+    static std::map<TuneKey, int> c;
+    return c;
+}
+
+void set_tile(ads_sim *s, int ty)
+{
+    const int pi = s->prec == ADS_FP64 ? 0 : 1;
+    if (s->ty[pi] == ty) return;
+    s->ty[pi] = ty;
+    s->fuse[pi] = ty == s->d.my;
+    drop_graphs(s);
+}
+
+// Time each candidate tile on the simulation itself for trial_steps steps
+// (after one untimed step), restoring state and step counter after every
+// trial; keep the fastest.  Results are cached per (grid, p, precision,
+// kind) for the process.
+int autotune(ads_sim *s, int trial_steps)
+{
+    const TuneKey key{s->d.mx, s->d.my, s->d.mz, s->p, s->prec, s->kind};
+    auto hit = tune_cache().find(key);
+    if (hit != tune_cache().end()) {
+        set_tile(s, hit->second);
+        return ADS_OK;
+    }
+    const std::vector<int> cand = tile_candidates(s);
+    if (cand.empty()) return fail(ADS_ERR_UNSUPPORTED, "ads_autotune: no tile fits shared memory");
+    if (cand.size() == 1 || trial_steps == 0) {
+        set_tile(s, cand[0]);
+        tune_cache()[key] = cand[0];
+        return ADS_OK;
+    }
+    // snapshot of everything a step writes
+    const size_t n = (size_t)s->d.count() * elem(s);
+    std::vector<std::pair<void *, size_t>> state;
+    if (s->kind == ADS_SCALAR_WAVE) state = {{s->P, n}, {s->Q, n}, {s->A, n}};
+    else state = {{s->U, 3 * n}, {s->Up, 3 * n}};
+    state.push_back({s->d_step, sizeof(long long)});
+    Scratch sc(s);
+    std::vector<void *> saved;
+    for (auto &st : state) {
+        void *b = sc.get(st.second);
+        if (!b) return fail(ADS_ERR_OOM, "ads_autotune: scratch allocation failed");
+        ADS_CK(cudaMemcpyAsync(b, st.first, st.second, cudaMemcpyDeviceToDevice, s->stream));
+        saved.push_back(b);
+    }
+    auto restore = [&]() -> int {
+        for (size_t i = 0; i < state.size(); ++i)
+            ADS_CK(cudaMemcpyAsync(state[i].first, saved[i], state[i].second, cudaMemcpyDeviceToDevice, s->stream));
+        return ADS_OK;
+    };
+    cudaEvent_t e0, e1;
+    ADS_CK(cudaEventCreate(&e0));
+    ADS_CK(cudaEventCreate(&e1));
+    const int orig = s->ty[s->prec == ADS_FP64 ? 0 : 1];
+    int best = cand[0], rc = ADS_OK;
+    float best_ms = 1e30f;
+    const unsigned long long launches = ads::g_launches;
+    for (int t : cand) {
+        set_tile(s, t);
+        if ((rc = step_once(s, false))) break;
+        cudaEventRecord(e0, s->stream);
+        for (int i = 0; i < trial_steps && rc == ADS_OK; ++i) rc = step_once(s, false);
+        cudaEventRecord(e1, s->stream);
+        if (rc || (rc = restore())) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail(ADS_ERR_CUDA, "ads_autotune: timing failed");
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    ads::g_launches = launches;   // trial launches are not part of any step
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        set_tile(s, orig);
+        return rc;
+    }
+    if ((rc = check_device_error(s))) return rc;
+    set_tile(s, best);
+    tune_cache()[key] = best;
     return ADS_OK;
 }
 
@@ -979,6 +1315,10 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
         if (q) cudaMemsetAsync(q, 0, n, s->stream);
     cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->stream);
     cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
+    static unsigned long long next_uid = 0;
+    s->uid = ++next_uid;
+    if (s->kind == ADS_SCALAR_WAVE)
+        s->has_maps = ads::make_update_maps(&s->upd_maps, s->P, s->Q, (int)elem(s), s->d, 2);
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
         ads_destroy(s);
         return fail(ADS_ERR_CUDA, "ads_create: initialisation failed");
@@ -1201,11 +1541,37 @@ int ads_step(ads_sim_t *s, int nsteps)
 
 int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps)
 {
-    if (!sims || count < 0) return fail(ADS_ERR_INVALID_ARG, "ads_batch_step: bad arguments");
+    if (!sims || count < 0 || nsteps < 0) return fail(ADS_ERR_INVALID_ARG, "ads_batch_step: bad arguments");
+    if (count == 0 || nsteps == 0) return ADS_OK;
     for (int i = 0; i < count; ++i) {
-        int rc = ads_step(sims[i], nsteps);
-        if (rc) return rc;
+        if (!sims[i]) return fail(ADS_ERR_INVALID_ARG, "ads_batch_step: null simulation");
+        if (sims[i]->device != sims[0]->device) return fail(ADS_ERR_INVALID_ARG, "ads_batch_step: mixed devices");
+        for (int j = 0; j < i; ++j)
+            if (sims[j] == sims[i]) return fail(ADS_ERR_INVALID_ARG, "ads_batch_step: a simulation appears twice");
     }
+    cudaSetDevice(sims[0]->device);
+    // scalar-wave simulations share grouped launches per (precision, degree);
+    // elasticity advances on each simulation's own stream meanwhile
+    std::map<std::pair<int, int>, std::vector<ads_sim *>> groups;
+    for (int i = 0; i < count; ++i) {
+        ads_sim *s = sims[i];
+        if (s->kind == ADS_SCALAR_WAVE) {
+            groups[{s->prec, s->p}].push_back(s);
+        } else {
+            int rc = ads_step(s, nsteps);
+            if (rc) return rc;
+        }
+    }
+    return batch_groups(groups, nsteps);
+}
+
+int ads_autotune(ads_sim_t *s, int trial_steps, int *tile_rows)
+{
+    if (!s || trial_steps < 0) return fail(ADS_ERR_INVALID_ARG, "ads_autotune: bad arguments");
+    cudaSetDevice(s->device);
+    int rc = autotune(s, trial_steps);
+    if (rc) return rc;
+    if (tile_rows) *tile_rows = s->ty[s->prec == ADS_FP64 ? 0 : 1];
     return ADS_OK;
 }
 
@@ -1337,6 +1703,50 @@ int ads_checkpoint_load(ads_sim_t *s, const void *host, size_t bytes)
 }
 
 size_t ads_device_bytes(const ads_sim_t *s) { return s ? s->bytes : 0; }
+
+size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision)
+{
+    if (!grid || p < 1 || p > 4 || (kind != ADS_SCALAR_WAVE && kind != ADS_ELASTIC) ||
+        (precision != ADS_FP64 && precision != ADS_FP32))
+        return 0;
+    size_t m[3], mp[3], S[3];
+    for (int a = 0; a < 3; ++a) {
+        const long long me = (long long)grid->n_elem[a] + p - 2;
+        if (grid->n_elem[a] < 1 || me < 1) return 0;
+        m[a] = (size_t)me;
+        S[a] = (m[a] + ads::kSeg - 1) / ads::kSeg;
+        mp[a] = S[a] * ads::kSeg;
+    }
+    const size_t W = 2 * (size_t)p + 1, el = precision == ADS_FP64 ? 8 : 4;
+    const size_t cnt = (m[0] + 7) / 8 * 8 * m[1] * m[2];
+    size_t b = 0;
+    // every allocation rounded up as a caching allocator would (512 B, 2 MiB above 1 MiB)
+    auto add = [&](size_t x) { b += x > (1u << 20) ? (x + (2u << 20) - 1) / (2u << 20) * (2u << 20) : (x + 511) / 512 * 512; };
+    add(sizeof(long long));
+    add(sizeof(int));
+    if (kind == ADS_SCALAR_WAVE) {
+        for (int i = 0; i < 4; ++i) add(cnt * el);
+    } else {
+        for (int i = 0; i < 4; ++i) add(3 * cnt * el);
+        add(cnt * el);
+        add(cnt * el);
+        for (int a = 0; a < 3; ++a) add(2 * mp[a] * W * 8);
+    }
+    const int nsets = kind == ADS_SCALAR_WAVE ? 3 : 4;
+    for (int t = 0; t < (precision == ADS_FP32 ? 2 : 1); ++t) {
+        const size_t e = t == 0 ? 8 : 4;
+        for (int a = 0; a < 3; ++a) {
+            add(3 * mp[a] * W * e + 64);                                    // M, K, B
+            for (int k = 0; k < nsets; ++k) add(ads::line_image_elems(p, (int)S[a]) * e + 64);
+            add(mp[a] * W * e);                                             // bands of M + eta K
+            add(mp[a] * e);                                                 // source load vector
+        }
+        for (int k = 0; k < nsets; ++k)
+            add(2 * (mp[0] + mp[1]) * W * e + (mp[0] + mp[1]) * e +
+                (ads::line_image_elems(p, (int)S[0]) + ads::line_image_elems(p, (int)S[1])) * e + 64);
+    }
+    return b;
+}
 
 }  // extern "C"
 

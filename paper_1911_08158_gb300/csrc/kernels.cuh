@@ -1,9 +1,13 @@
 // kernels.cuh -- launch interface of the device kernels (sm_103a).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace ads {
+
+constexpr int kSeg = 32;     // rows per register segment of the line solves
+constexpr int kBatch = 32;   // simulations per grouped launch
 
 // Interior field layout on the device: [z][y][x], x fastest, row pitch sx
 // elements (sx >= mx, padding kept at zero), plane pitch sx*my.
@@ -87,6 +91,38 @@ struct ColArgs {
     int *err;             // device error word (bounded waits)
 };
 
+// TMA maps of the (p, q) state arrays for the K3 epilogue: 3D maps over
+// [z][y][x] with a box of 32 columns x col_box(len) rows along the axis.
+struct ColMaps {
+    CUtensorMap P, Q;
+};
+
+// rows per TMA box along a line of length len (at most 256, equal chunks)
+inline int col_box(int len)
+{
+    const int nch = (len + 255) / 256;
+    return (len + nch - 1) / nch;
+}
+bool make_update_maps(ColMaps *m, const void *P, const void *Q, int elem, const Dims &d, int axis);
+
+// Kernel parameter blocks of a grouped launch: NB simulations, block b of
+// the flat grid belongs to simulation i with off[i] <= b < off[i+1].
+template <typename T, int NB>
+struct RhsGroup {
+    RhsArgs<T> a[NB];
+    int off[NB + 1];
+    int n;
+};
+
+template <typename T, int NB>
+struct ColGroup {
+    ColMaps maps[NB];
+    ColArgs<T> a[NB];
+    int box[NB];
+    int off[NB + 1];
+    int n;
+};
+
 // seg: register segment width of the partitioned solves (32)
 size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy);
 int rhs_threads(int elem);
@@ -99,6 +135,13 @@ template <typename T>
 cudaError_t launch_rhs(int p, int seg, const RhsArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_col(int p, int seg, const ColArgs<T> &a, cudaStream_t s);
+// Grouped launches: n independent simulations of degree p (any grids) in
+// ceil(n / kBatch) launches; maps (nullable) holds precomputed update maps
+// per entry (mode 1), else they are encoded here.
+template <typename T>
+cudaError_t launch_rhs_group(int p, const RhsArgs<T> *a, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s);
 
 // out = band applied along axis (0,1,2) to in; out = beta*out + alpha*(A in)
 template <typename T>

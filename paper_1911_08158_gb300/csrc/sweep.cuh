@@ -1,0 +1,843 @@
+// sweep.cuh -- the hot-path kernels of the scalar-wave step (sm_103a) and
+// their grouped launchers.  Included only by the translation units that
+// instantiate them (rhs_f32.cu, rhs_f64.cu, col_f32.cu, col_f64.cu).
+//
+// Hot path of one scalar-wave step (Sec. 2, eq. pwave2; Appendix):
+//   K1  k_rhs   : sum-factorised RHS  F(t_{n+1}) - K p_n  on a tile of x-lines,
+//                 then the x-direction banded forward/back substitution of
+//                 (Mx + eta Kx) on every line of the tile, and the y-direction
+//                 sweep when a tile spans the whole y extent (then K2 is skipped);
+//   K2  k_col(y): y-direction sweep, 32 x-columns per CTA, coalesced rows;
+//   K3  k_col(z): z-direction sweep + Newmark update of the (p, q) state.
+// Every kernel takes a group of up to NB independent simulations (same
+// degree and precision, any grid): the flat block index is split into
+// per-simulation ranges (RhsGroup::off / ColGroup::off), so one launch
+// advances a whole batch; NB = 1 is the single-simulation launch.
+#pragma once
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tma.cuh"
+
+namespace ads {
+namespace {
+
+
+// ---------------------------------------------------------------- shared helpers
+
+// cooperative copy of n elements global -> shared
+template <typename T>
+__device__ __forceinline__ void stage(T *dst, const T *src, int n, int tid, int nt)
+{
+    for (int i = tid; i < n; i += nt) dst[i] = src[i];
+}
+
+// Shared-memory image of the tables of one directional factor set.
+template <typename T>
+struct LineSm {
+    T *fac, *phi, *psi, *Phi, *Psi;
+    int S;
+};
+
+template <typename T, int P>
+__host__ __device__ __forceinline__ size_t line_sm_elems(int m, int S)
+{
+    return (size_t)m * (2 * P + 1) + 2 * (size_t)m * P + 2 * (size_t)S * P * P;
+}
+
+// pointers into a shared-memory copy of a LineDev buffer (m = S * SEG rows)
+template <typename T, int P>
+__device__ __forceinline__ LineSm<T> line_carve(T *base, int m, int S)
+{
+    LineSm<T> l;
+    l.S = S;
+    l.fac = base; base += (size_t)m * (2 * P + 1);
+    l.phi = base; base += (size_t)m * P;
+    l.psi = base; base += (size_t)m * P;
+    l.Phi = base; base += (size_t)S * P * P;
+    l.Psi = base;
+    return l;
+}
+
+
+// ------------------------------------------------ segment-parallel solve
+//
+// A line of length m is cut into segments of SEG rows (the last may be
+// shorter).  The thread owning segment s keeps its rows in registers
+// v[0..SEG) (rows s*SEG + k; v[k] = 0 past the line end) and runs:
+//   pass 1  local forward substitution with zero carry-in
+//   (carry)  c_s = sum over earlier segments through the transfer matrices Phi
+//   pass 2  forward correction v += sum_k c_s[k] phi[.][k], fused with the
+//           local backward substitution (zero carry-in from below)
+//   (carry)  e_s through Psi from later segments
+//   pass 3  backward correction v += sum_k e_s[k] psi[.][k]
+// which equals plain forward/back substitution of the banded LU (Appendix)
+// up to rounding order.  Every loop is fully unrolled over SEG, so each
+// element of v is a register.
+
+// The 1D tables are padded to whole segments (identity factor rows, zero
+// fundamental solutions beyond the line end), so every segment is full and
+// the passes need no predicates.  fb/pb: the segment's rows of fac/phi.
+template <typename T, int P, int SEG>
+__device__ __forceinline__ void seg_pass1(const T *fb, T (&v)[SEG])
+{
+    constexpr int W = 2 * P + 1;
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) {
+        T w = v[k];
+#pragma unroll
+        for (int q = 1; q <= P; ++q)
+            if (k - q >= 0) w -= fb[k * W + P - q] * v[k - q];
+        v[k] = w;
+    }
+}
+
+template <typename T, int P, int SEG>
+__device__ __forceinline__ void seg_pass2(const T *fb, const T *pb, const T (&c)[P], T (&v)[SEG])
+{
+    constexpr int W = 2 * P + 1;
+#pragma unroll
+    for (int k = SEG - 1; k >= 0; --k) {
+        T w = v[k];
+#pragma unroll
+        for (int q = 0; q < P; ++q) w += c[q] * pb[k * P + q];
+#pragma unroll
+        for (int q = 1; q <= P; ++q)
+            if (k + q < SEG) w -= fb[k * W + P + q] * v[k + q];
+        v[k] = w * fb[k * W + P];
+    }
+}
+
+template <typename T, int P, int SEG>
+__device__ __forceinline__ void seg_pass3(const T *qb, const T (&e)[P], T (&v)[SEG])
+{
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) {
+        T x = v[k];
+#pragma unroll
+        for (int q = 0; q < P; ++q) x += e[q] * qb[k * P + q];
+        v[k] = x;
+    }
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void carry_fwd(const T *Phi, int s, const T *CT, int ld, int j, T (&c)[P])
+{
+#pragma unroll
+    for (int k = 0; k < P; ++k) c[k] = T(0);
+    for (int q = 0; q < s; ++q) {
+        T n[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            T acc = CT[(q * P + k) * ld + j];
+#pragma unroll
+            for (int r = 0; r < P; ++r) acc += Phi[(q * P + k) * P + r] * c[r];
+            n[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < P; ++k) c[k] = n[k];
+    }
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void carry_bwd(const T *Psi, int S, int s, const T *CH, int ld, int j, T (&e)[P])
+{
+#pragma unroll
+    for (int k = 0; k < P; ++k) e[k] = T(0);
+    for (int q = S - 1; q > s; --q) {
+        T n[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            T acc = CH[(q * P + k) * ld + j];
+#pragma unroll
+            for (int r = 0; r < P; ++r) acc += Psi[(q * P + k) * P + r] * e[r];
+            n[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < P; ++k) e[k] = n[k];
+    }
+}
+
+// Passes 2-3 with the two carry exchanges, after pass 1 left v in
+// registers.  All threads of the block call it (it synchronises); `on`
+// marks threads that own a segment.  CT/CH: [S][P][ld], slot j.
+template <typename T, int P, int SEG>
+__device__ __forceinline__ void seg_finish(const LineSm<T> &L, bool on, int s, int j, int ld, T *CT, T *CH,
+                                           T (&v)[SEG])
+{
+    constexpr int W = 2 * P + 1;
+    const int b0 = s * SEG;
+    if (on) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) CT[(s * P + k) * ld + j] = v[SEG - 1 - k];
+    }
+    __syncthreads();
+    if (on) {
+        T c[P];
+        carry_fwd<T, P>(L.Phi, s, CT, ld, j, c);
+        seg_pass2<T, P, SEG>(L.fac + b0 * W, L.phi + b0 * P, c, v);
+#pragma unroll
+        for (int k = 0; k < P; ++k) CH[(s * P + k) * ld + j] = v[k];
+    }
+    __syncthreads();
+    if (on) {
+        T e[P];
+        carry_bwd<T, P>(L.Psi, L.S, s, CH, ld, j, e);
+        seg_pass3<T, P, SEG>(L.psi + b0 * P, e, v);
+    }
+}
+
+// band row of a Toeplitz-interior band: registers inside [lo, hi), table outside
+template <typename T, int W>
+__device__ __forceinline__ void band_row(const T *tab, int lo, int hi, const T (&mid)[W], int i, T (&r)[W])
+{
+    if (i >= lo && i < hi) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) r[k] = mid[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) r[k] = tab[i * W + k];
+    }
+}
+
+// Phase 1 of K1 for the column pair (x, x+1) and output rows [yb, ye):
+// stream the rows yp = yb-P .. ye+P-1, z-contract each (t1 = Mz p,
+// t2 = Kz p) into a ring of W slots, and y-contract every complete window
+// into s1, s2.  The loop is unrolled by W so that ring slots are static
+// registers.  GUARD: rows or planes may fall outside the grid (zero);
+// INTERIOR: every output row lies in the Toeplitz range (band rows from
+// registers).  Column x+1 may be the zero padding of the row (x+1 = mx).
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> { using type = float2; };
+template <>
+struct Vec2<double> { using type = double2; };
+
+template <typename T, int P, bool GUARD, bool INTERIOR>
+__device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int sx, int my, const bool (&zok)[2 * P + 1],
+                                             const T (&cm)[2 * P + 1], const T (&ck)[2 * P + 1],
+                                             const T (&mym)[2 * P + 1], const T (&myk)[2 * P + 1], const T *bMy,
+                                             const T *bKy, int ylo, int yhi, int yb, int ye, T *s1col, T *s2col, int RS)
+{
+    constexpr int W = 2 * P + 1;
+    using V2 = typename Vec2<T>::type;
+    T r1[W][2], r2[W][2];
+#pragma unroll
+    for (int k = 0; k < W; ++k) r1[k][0] = r1[k][1] = r2[k][0] = r2[k][1] = T(0);
+    const int n = ye - yb + 2 * P;
+    const T *rowp = col0 + (long long)(yb - P) * sx;
+    for (int r0 = 0; r0 < n; r0 += W) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int r = r0 + j;
+            const int yp = yb - P + r;
+            const bool ok = GUARD ? ((r < n) && yp >= 0 && yp < my) : (r < n);
+            const T *c = rowp + (long long)r * sx;
+            V2 v[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const bool okk = GUARD ? (ok && zok[k]) : ok;
+                v[k] = okk ? *reinterpret_cast<const V2 *>(c + (long long)k * plane) : V2{T(0), T(0)};
+            }
+            T t10 = T(0), t11 = T(0), t20 = T(0), t21 = T(0);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                t10 += cm[k] * v[k].x;
+                t11 += cm[k] * v[k].y;
+                t20 += ck[k] * v[k].x;
+                t21 += ck[k] * v[k].y;
+            }
+            r1[j][0] = t10; r1[j][1] = t11;
+            r2[j][0] = t20; r2[j][1] = t21;
+            if (r >= 2 * P && r < n) {
+                const int y = yb + r - 2 * P;
+                T bm[W], bk[W];
+                if (INTERIOR) {
+#pragma unroll
+                    for (int q = 0; q < W; ++q) { bm[q] = mym[q]; bk[q] = myk[q]; }
+                } else {
+                    band_row<T, W>(bMy, ylo, yhi, mym, y, bm);
+                    band_row<T, W>(bKy, ylo, yhi, myk, y, bk);
+                }
+                T a0 = T(0), a1 = T(0), c0 = T(0), c1 = T(0);
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    // window row y-P+q = stream index r-2P+q  ->  ring slot (j-2P+q) mod W
+                    const int sl = (j - 2 * P + q + 2 * W) % W;
+                    a0 += bm[q] * r1[sl][0];
+                    a1 += bm[q] * r1[sl][1];
+                    c0 += bk[q] * r1[sl][0] + bm[q] * r2[sl][0];
+                    c1 += bk[q] * r1[sl][1] + bm[q] * r2[sl][1];
+                }
+                s1col[(size_t)y * RS] = a0;
+                s1col[(size_t)y * RS + 1] = a1;
+                s2col[(size_t)y * RS] = c0;
+                s2col[(size_t)y * RS + 1] = c1;
+            }
+        }
+    }
+}
+
+// Phase 2 of K1, pass 1 for one row segment [b0, b0+n): form
+//   R = F - c2 (Kx s1 + Mx s2)
+// from the s1, s2 rows with a static register window and run the local
+// forward substitution on it.  FAST: a full segment inside the Toeplitz
+// range (no predicates, band rows in registers).
+// Segment kinds of the x-direction pass 1.
+enum { kSegMiddle = 0, kSegFirst = 1, kSegLast = 2, kSegGeneral = 3 };
+constexpr int kHeadRows = 8;   // leading rows of the first segment read from the band table (>= Toeplitz lo)
+
+template <typename T, int P, int SEG, int MODE>
+__device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx, int b0, const T (&mxm)[2 * P + 1],
+                                           const T (&mxk)[2 * P + 1], const T *bMx, const T *bKx, int xlo, int xhi,
+                                           const T *fb, const T *fx, T rowF, T c2, T (&v)[SEG])
+{
+    constexpr int W = 2 * P + 1;
+    T a1[SEG + 2 * P], a2[SEG + 2 * P];   // window positions b0-P .. b0+SEG+P-1 (static after unrolling)
+#pragma unroll
+    for (int j = 0; j < SEG + 2 * P; ++j) {
+        const int xx = b0 - P + j;
+        bool in_;
+        if (MODE == kSegMiddle) in_ = true;
+        else if (MODE == kSegFirst) in_ = j >= P;                  // x < 0 is outside
+        else if (MODE == kSegLast) in_ = xx < mx;                  // b0 - P >= 0 here
+        else in_ = xx >= 0 && xx < mx;
+        a1[j] = in_ ? row1[xx] : T(0);
+        a2[j] = in_ ? row2[xx] : T(0);
+    }
+    const T *fxb = fx ? fx + b0 : nullptr;
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) {
+        const int x = b0 + k;
+        T bm[W], bk[W];
+        const bool table = MODE == kSegLast || (MODE == kSegFirst && k < kHeadRows);
+        if (MODE == kSegGeneral) {
+            band_row<T, W>(bMx, xlo, xhi, mxm, x, bm);   // rows past the line end are zero
+            band_row<T, W>(bKx, xlo, xhi, mxk, x, bk);
+        } else if (table) {
+#pragma unroll
+            for (int q = 0; q < W; ++q) { bm[q] = bMx[x * W + q]; bk[q] = bKx[x * W + q]; }
+        } else {
+#pragma unroll
+            for (int q = 0; q < W; ++q) { bm[q] = mxm[q]; bk[q] = mxk[q]; }
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc += bk[q] * a1[k + q] + bm[q] * a2[k + q];
+        T w = (fxb ? rowF * fxb[k] : T(0)) - c2 * acc;
+#pragma unroll
+        for (int q = 1; q <= P; ++q)
+            if (k - q >= 0) w -= fb[k * W + P - q] * v[k - q];
+        v[k] = w;
+    }
+}
+
+// ---------------------------------------------------------------- K1
+//
+// One CTA per (z-plane, y-tile of ty rows).  Shared memory: S1, S2 [ty][RS]
+// (RS odd), carry buffers and the 1D tables.  Phases:
+//  1. z- then y-contraction of p, thread per x, streaming along y with a
+//     register window (loads prefetched two rows ahead):
+//        s1 = (My.Mz) p,   s2 = (Ky.Mz + My.Kz) p       (K p = Kx s1 + Mx s2)
+//  2. x-direction, thread per (row, segment of SEG): R = F - c2 (Kx s1 + Mx s2)
+//     is formed in registers while the local forward pass runs, then the
+//     carry exchange and passes 2-3; the row is written back to S1.
+//  3. whole plane in the tile: y-direction solve, thread per (x, segment).
+//  4. coalesced store.
+template <typename T>
+struct RhsThreads {
+    static constexpr int value = sizeof(T) == 8 ? 256 : 512;   // FP64: more registers per thread
+};
+
+// index of the simulation that owns block b: off[i] <= b < off[i+1]
+__device__ __forceinline__ int group_find(const int *off, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int P, int NB>
+__global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_constant__ RhsGroup<T, NB> g)
+{
+    const int gs = NB > 1 ? group_find(g.off, g.n, blockIdx.x) : 0;
+    const RhsArgs<T> &a = g.a[gs];
+    const int lb = blockIdx.x - g.off[gs];   // block within this simulation
+    constexpr int W = 2 * P + 1;
+    constexpr int SEG = kSeg;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ T s_r;
+    const int mx = a.d.mx, my = a.d.my, mz = a.d.mz, sx = a.d.sx;
+    const long long plane = (long long)sx * my;
+    const int RS = ((mx + 1) & ~1) | 1;   // odd, holds every column pair
+    const int ty = a.ty;
+    const int nty = (my + ty - 1) / ty;
+    const int y0 = (lb % nty) * ty, z = lb / nty;
+    const int tye = min(ty, my - y0);
+    const bool fuse_y = (ty == my);
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
+    const int rows_pad = (ty + 31) & ~31, cols_pad = (mx + 31) & ~31;
+    const int cld = (fuse_y && cols_pad > rows_pad) ? cols_pad : rows_pad;
+
+    __shared__ __align__(8) uint64_t bar;
+    T *S1 = reinterpret_cast<T *>(smem_raw);
+    T *S2 = S1 + (size_t)ty * RS;
+    const int Smax = (fuse_y && a.ly.S > a.lx.S) ? a.ly.S : a.lx.S;
+    T *CT = S2 + (size_t)ty * RS;
+    T *CH = CT + (size_t)Smax * P * cld;
+    // the 1D tables arrive as one bulk copy into a 16-byte aligned region
+    T *tb = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(CH + (size_t)Smax * P * cld) + 15) & ~(uintptr_t)15);
+    const int mxp = a.lx.S * SEG, myp = a.ly.S * SEG;   // padded table lengths
+    T *bMx = tb;
+    T *bKx = bMx + mxp * W;
+    T *bMy = bKx + mxp * W;
+    T *bKy = bMy + myp * W;
+    T *sfx = bKy + myp * W;
+    T *sfy = sfx + mxp;
+    T *lxb = sfy + myp;
+    T *lyb = lxb + line_image_elems_dev(P, mxp, a.lx.S);
+    const LineSm<T> LX = line_carve<T, P>(lxb, mxp, a.lx.S);
+    const LineSm<T> LY = line_carve<T, P>(lyb, myp, a.ly.S);
+    const bool has_src = a.src.fx != nullptr;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(&bar, (uint32_t)a.img_bytes);
+        bulk_load(tb, a.img, (uint32_t)a.img_bytes, &bar);
+        T r = T(0);
+        if (has_src) {   // overlaps the copy
+            double t = (double)(a.step[0] + a.toff) * a.tau;
+            r = (T)(a.src.amp * ricker_dev(a.src.freq, a.src.t0, t));
+        }
+        s_r = r;
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0, a.err)) return;   // error recorded for the host
+
+    // ---- phase 1
+    {
+        T cm[W], ck[W], mym[W], myk[W];
+        const int ylo = a.bandM[1].lo, yhi = a.bandM[1].hi;   // K shares M's interior range
+        bool zok[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            cm[k] = a.bandM[2].v[z * W + k];
+            ck[k] = a.bandK[2].v[z * W + k];
+            const int mid = ylo < yhi ? ylo : 0;
+            mym[k] = bMy[mid * W + k];
+            myk[k] = bKy[mid * W + k];
+            zok[k] = (z + k - P >= 0) && (z + k - P < mz);
+        }
+        const int npair = (mx + 1) >> 1;          // column pairs (the last may end in padding)
+        const int XG = (npair + 31) >> 5;
+        int YC = nwarps / XG;
+        if (YC < 1) YC = 1;
+        const int rows_per = (tye + YC - 1) / YC;
+        const bool zin = z >= P && z + P < mz;
+        for (int item = warp; item < XG * YC; item += nwarps) {
+            const int xg = item % XG, yc = item / XG;
+            const int pr = xg * 32 + lane;
+            const int x = 2 * pr;
+            const int yb = y0 + yc * rows_per;
+            int ye = yb + rows_per;
+            if (ye > y0 + tye) ye = y0 + tye;
+            if (yb >= ye || pr >= npair) continue;
+            const T *col0 = a.in + x + (long long)(z - P) * plane;   // plane z-P, row 0, column x
+            T *c1 = S1 + x - (size_t)y0 * RS, *c2 = S2 + x - (size_t)y0 * RS;
+            const bool guard = !zin || yb - P < 0 || ye + P > my;
+            const bool inter = yb >= ylo && ye <= yhi;
+            if (!guard && inter)
+                phase1_chunk<T, P, false, true>(col0, plane, sx, my, zok, cm, ck, mym, myk, bMy, bKy, ylo, yhi, yb, ye, c1, c2, RS);
+            else if (!guard)
+                phase1_chunk<T, P, false, false>(col0, plane, sx, my, zok, cm, ck, mym, myk, bMy, bKy, ylo, yhi, yb, ye, c1, c2, RS);
+            else
+                phase1_chunk<T, P, true, false>(col0, plane, sx, my, zok, cm, ck, mym, myk, bMy, bKy, ylo, yhi, yb, ye, c1, c2, RS);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: x-direction, thread per (row, segment); rounds of row groups
+    const int RG = rows_pad >> 5;
+    const int gpr2 = nwarps / LX.S > 0 ? nwarps / LX.S : 1;
+    for (int g0 = 0; g0 < RG; g0 += gpr2) {
+        const int gi = warp / LX.S, s = warp % LX.S;
+        const int g = g0 + gi;
+        const int l = g * 32 + lane;
+        const bool on = gi < gpr2 && g < RG && l < tye;
+        const int b0 = s * SEG;
+        const int n = on ? min(SEG, mx - b0) : 0;
+        T v[SEG];
+#pragma unroll
+        for (int k = 0; k < SEG; ++k) v[k] = T(0);
+        if (on) {
+            const T *row1 = S1 + (size_t)l * RS;
+            const T *row2 = S2 + (size_t)l * RS;
+            const int y = y0 + l;
+            const T rowF = has_src ? s_r * sfy[y] * a.src.fz[z] : T(0);
+            const T c2 = a.c2;
+            const int xlo = a.bandM[0].lo, xhi = a.bandM[0].hi;
+            T mxm[W], mxk[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const int mid = xlo < xhi ? xlo : 0;
+                mxm[k] = bMx[mid * W + k];
+                mxk[k] = bKx[mid * W + k];
+            }
+            const T *srcF = has_src ? sfx : nullptr;
+            const T *fb = LX.fac + b0 * W;
+            // kinds: interior segments take bands from registers; the first reads its
+            // head rows (< kHeadRows >= Toeplitz lo) from the table; the last reads
+            // every row from the table (its rows past hi are not Toeplitz)
+            const bool regular = LX.S >= 2 && xlo <= kHeadRows && xhi >= (LX.S - 1) * SEG && mx >= (LX.S - 1) * SEG + P;
+            if (regular && s > 0 && s < LX.S - 1)
+                phase2_fwd<T, P, SEG, kSegMiddle>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
+            else if (regular && s == 0)
+                phase2_fwd<T, P, SEG, kSegFirst>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
+            else if (regular)
+                phase2_fwd<T, P, SEG, kSegLast>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
+            else
+                phase2_fwd<T, P, SEG, kSegGeneral>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
+        }
+        seg_finish<T, P, SEG>(LX, on, s, l, cld, CT, CH, v);   // reads of S1/S2 are done (its first barrier)
+        if (on) {
+            T *row1 = S1 + (size_t)l * RS;
+#pragma unroll
+            for (int k = 0; k < SEG; ++k)
+                if (k < n) row1[b0 + k] = v[k];
+        }
+        __syncthreads();
+    }
+
+    // ---- phase 3: y-direction (whole plane), thread per (x, segment); rounds of column groups
+    if (fuse_y) {
+        const int CG = cols_pad >> 5;
+        const int gpr3 = nwarps / LY.S > 0 ? nwarps / LY.S : 1;
+        for (int g0 = 0; g0 < CG; g0 += gpr3) {
+            const int gi = warp / LY.S, s = warp % LY.S;
+            const int x = (g0 + gi) * 32 + lane;
+            const bool on = gi < gpr3 && x < mx;
+            const int b0 = s * SEG;
+            const int n = on ? min(SEG, my - b0) : 0;
+            T v[SEG];
+#pragma unroll
+            for (int k = 0; k < SEG; ++k) v[k] = (k < n) ? S1[(size_t)(b0 + k) * RS + x] : T(0);
+            if (on) seg_pass1<T, P, SEG>(LY.fac + b0 * W, v);
+            seg_finish<T, P, SEG>(LY, on, s, x, cld, CT, CH, v);
+            if (on) {
+#pragma unroll
+                for (int k = 0; k < SEG; ++k)
+                    if (k < n) S1[(size_t)(b0 + k) * RS + x] = v[k];
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- phase 4: store
+    {
+        T *dst0 = a.out + (long long)z * plane + (long long)y0 * sx;
+        for (int l = warp; l < tye; l += nwarps) {
+            const T *src = S1 + (size_t)l * RS;
+            T *dst = dst0 + (long long)l * sx;
+            for (int x = lane; x < mx; x += 32) dst[x] = src[x];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- K2/K3
+//
+// 32 x-columns per CTA (lane = column), one warp per line segment of SEG
+// rows held in registers (coalesced direct loads: a warp reads 32
+// consecutive values of each row).  Epilogue: plain store, or the Newmark
+// update of the (p, q) state, whose p and q tiles [len][32] are fetched by
+// TMA at kernel start (overlapping the solve), updated in shared memory and
+// written back by TMA stores.
+template <typename T, int P, int NB>
+__global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T, NB> g)
+{
+    const int gs = NB > 1 ? group_find(g.off, g.n, blockIdx.x) : 0;
+    const ColArgs<T> &a = g.a[gs];
+    const ColMaps &maps = g.maps[gs];
+    const int box = g.box[gs];
+    const int blk = blockIdx.x - g.off[gs];   // block within this simulation
+    constexpr int SEG = kSeg;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    const Dims d = a.d;
+    const int tid = threadIdx.x, lane = tid & 31, s = tid >> 5;
+    const int ntx = (d.mx + 31) >> 5;
+    const int x0 = (blk % ntx) * 32, x = x0 + lane;
+    const int o = blk / ntx;
+    int len;
+    long long stride, base;
+    if (a.axis == 1) {
+        len = d.my;
+        stride = d.sx;
+        base = (long long)o * d.plane();
+    } else {
+        len = d.mz;
+        stride = d.plane();
+        base = (long long)o * d.sx;
+    }
+    __shared__ __align__(8) uint64_t bar_tab;
+    const bool upd = a.mode == 1;
+    const int nch = upd ? (len + box - 1) / box : 0;
+    const int rows = nch * box;
+    unsigned char *sm = align128(smem_raw);   // the host reserves 128 spare bytes
+    T *bufP = reinterpret_cast<T *>(sm);
+    T *bufQ = bufP + (size_t)rows * 32;
+    T *CT = bufQ + (size_t)rows * 32;
+    T *CH = CT + (size_t)a.ln.S * P * 32;
+    T *lb = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(CH + (size_t)a.ln.S * P * 32) + 15) & ~(uintptr_t)15);
+    auto coords = [&](int c, int &c0, int &c1, int &c2) {
+        c0 = x0;
+        if (a.axis == 1) { c1 = c * box; c2 = o; }
+        else { c1 = o; c2 = c * box; }
+    };
+    if (tid == 0) {
+        mbar_init(&bar_tab, 1);
+        if (upd) mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(&bar_tab, (uint32_t)a.ln.bytes);
+        bulk_load(lb, a.ln.base, (uint32_t)a.ln.bytes, &bar_tab);
+        if (upd) {
+            mbar_expect_tx(&bar, 2u * nch * 32u * box * sizeof(T));
+            for (int c = 0; c < nch; ++c) {
+                int c0, c1, c2;
+                coords(c, c0, c1, c2);
+                tma_load_3d(bufP + (size_t)c * box * 32, &maps.P, &bar, c0, c1, c2);
+                tma_load_3d(bufQ + (size_t)c * box * 32, &maps.Q, &bar, c0, c1, c2);
+            }
+            if (blk == 0) a.step[0] += 1;
+        }
+    }
+    const bool on = x < d.mx && s < a.ln.S;
+    const int b0 = s * SEG;
+    const int n = on ? min(SEG, len - b0) : 0;
+    T v[SEG];
+    const T *__restrict__ in = a.in + base + x + (long long)b0 * stride;
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) v[k] = (k < n) ? in[(long long)k * stride] : T(0);
+    const LineSm<T> L = line_carve<T, P>(lb, a.ln.S * SEG, a.ln.S);
+    __syncthreads();   // barriers initialised
+    if (!mbar_wait_bounded(&bar_tab, 0, a.err)) return;
+    if (on) seg_pass1<T, P, SEG>(L.fac + b0 * (2 * P + 1), v);
+    seg_finish<T, P, SEG>(L, on, s, lane, 32, CT, CH, v);
+    const long long off = base + x + (long long)b0 * stride;
+    if (!upd) {
+        if (!on) return;
+        T *__restrict__ out = a.out + off;
+#pragma unroll
+        for (int k = 0; k < SEG; ++k)
+            if (k < n) out[(long long)k * stride] = v[k];
+        return;
+    }
+    if (!mbar_wait_bounded(&bar, 0, a.err)) return;   // error recorded for the host
+    if (on) {
+        const T tau2 = a.tau2;
+#pragma unroll
+        for (int k = 0; k < SEG; ++k) {
+            if (k < n) {
+                const int idx = (b0 + k) * 32 + lane;
+                const T q = bufQ[idx] + tau2 * v[k];
+                bufQ[idx] = q;
+                bufP[idx] += q;
+            }
+        }
+        if (a.write_a) {
+            T *__restrict__ Ap = a.A + off;
+#pragma unroll
+            for (int k = 0; k < SEG; ++k)
+                if (k < n) Ap[(long long)k * stride] = v[k];
+        }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+        for (int c = 0; c < nch; ++c) {
+            int c0, c1, c2;
+            coords(c, c0, c1, c2);
+            tma_store_3d(&maps.P, bufP + (size_t)c * box * 32, c0, c1, c2);
+            tma_store_3d(&maps.Q, bufQ + (size_t)c * box * 32, c0, c1, c2);
+        }
+        tma_store_commit();
+        tma_store_wait_read();
+    }
+}
+
+
+// ---------------------------------------------------------------- launchers
+
+template <typename T>
+bool rhs_entry_ok(const RhsArgs<T> &a)
+{
+    return a.d.mx > 0 && a.d.my > 0 && a.d.mz > 0 && a.ty > 0 && a.ty <= a.d.my && a.lx.S <= 16 &&
+           a.ly.S <= 16 && a.lx.S * kSeg >= a.d.mx && a.ly.S * kSeg >= a.d.my && a.img && !(a.img_bytes & 15) &&
+           !((uintptr_t)a.img & 15);
+}
+
+template <typename T>
+int rhs_blocks(const RhsArgs<T> &a)
+{
+    return (a.d.my + a.ty - 1) / a.ty * a.d.mz;
+}
+
+// one launch of up to NB simulations, entries a[order[0..n)]
+template <typename T, int P, int NB>
+cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream_t s)
+{
+    RhsGroup<T, NB> g;
+    std::memset(&g, 0, sizeof(g));
+    size_t smem = 0;
+    long long blocks = 0;
+    for (int k = 0; k < n; ++k) {
+        const RhsArgs<T> &e = a[order[k]];
+        if (!rhs_entry_ok(e)) return cudaErrorInvalidValue;
+        g.a[k] = e;
+        g.off[k] = (int)blocks;
+        blocks += rhs_blocks(e);
+        smem = std::max(smem, rhs_smem_bytes(P, sizeof(T), e.d, e.ty, e.lx.S, e.ly.S));
+    }
+    if (blocks <= 0 || blocks > (1ll << 30)) return cudaErrorInvalidValue;
+    g.off[n] = (int)blocks;
+    g.n = n;
+    static size_t smem_set = 48 * 1024;   // per instantiation: opt-in dynamic shared memory
+    if (smem > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_rhs<T, P, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    k_rhs<T, P, NB><<<(unsigned)blocks, RhsThreads<T>::value, smem, s>>>(g);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+template <typename T, int P>
+cudaError_t rhs_group_dispatch(const RhsArgs<T> *a, int n, cudaStream_t s)
+{
+    if (n == 1) {
+        const int o = 0;
+        return rhs_group_p<T, P, 1>(a, &o, 1, s);
+    }
+    // heaviest blocks first (rows x columns of a tile) so that the tail of
+    // the launch holds the short ones
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
+        return (long long)a[i].ty * a[i].d.mx > (long long)a[j].ty * a[j].d.mx;
+    });
+    for (int k0 = 0; k0 < n; k0 += kBatch) {
+        cudaError_t e = rhs_group_p<T, P, kBatch>(a, order.data() + k0, std::min(kBatch, n - k0), s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+bool col_entry_ok(const ColArgs<T> &a)
+{
+    const int len = a.axis == 1 ? a.d.my : a.d.mz;
+    return (a.axis == 1 || a.axis == 2) && a.d.mx > 0 && len > 0 && a.ln.S * kSeg >= len && a.ln.S <= 16 &&
+           a.ln.base && !(a.ln.bytes & 15) && !((uintptr_t)a.ln.base & 15) && (a.mode == 0 || a.mode == 1);
+}
+
+template <typename T, int P, int NB>
+cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *order, int n, cudaStream_t s)
+{
+    ColGroup<T, NB> g;
+    std::memset(&g, 0, sizeof(g));
+    size_t smem = 0;
+    long long blocks = 0;
+    int smax = 1;
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        const ColArgs<T> &e = a[i];
+        if (!col_entry_ok(e)) return cudaErrorInvalidValue;
+        const int len = e.axis == 1 ? e.d.my : e.d.mz;
+        const int outer = e.axis == 1 ? e.d.mz : e.d.my;
+        const int box = col_box(len);
+        size_t tiles = 0;
+        if (e.mode == 1) {
+            if (maps) g.maps[k] = maps[i];
+            else if (!make_update_maps(&g.maps[k], e.P, e.Q, sizeof(T), e.d, e.axis)) return cudaErrorInvalidValue;
+            tiles = 2 * (size_t)((len + box - 1) / box) * box * 32 * sizeof(T);
+        }
+        g.a[k] = e;
+        g.box[k] = box;
+        g.off[k] = (int)blocks;
+        blocks += (long long)((e.d.mx + 31) / 32) * outer;
+        smem = std::max(smem, 128 + tiles + col_smem_bytes(P, sizeof(T), len, e.ln.S));
+        smax = std::max(smax, e.ln.S);
+    }
+    if (blocks <= 0 || blocks > (1ll << 30)) return cudaErrorInvalidValue;
+    g.off[n] = (int)blocks;
+    g.n = n;
+    static size_t smem_set = 48 * 1024;
+    if (smem > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_col<T, P, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    k_col<T, P, NB><<<(unsigned)blocks, 32 * smax, smem, s>>>(g);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+template <typename T, int P>
+cudaError_t col_group_dispatch(const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s)
+{
+    if (n == 1) {
+        const int o = 0;
+        return col_group_p<T, P, 1>(a, maps, &o, 1, s);
+    }
+    auto len = [&](int i) { return a[i].axis == 1 ? a[i].d.my : a[i].d.mz; };
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return len(i) > len(j); });
+    for (int k0 = 0; k0 < n; k0 += kBatch) {
+        cudaError_t e = col_group_p<T, P, kBatch>(a, maps, order.data() + k0, std::min(kBatch, n - k0), s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+#define ADS_DISPATCH_P(p, CALL)                      \
+    switch (p) {                                     \
+    case 1: return CALL(1);                          \
+    case 2: return CALL(2);                          \
+    case 3: return CALL(3);                          \
+    case 4: return CALL(4);                          \
+    default: return cudaErrorInvalidValue;           \
+    }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_rhs_group(int p, const RhsArgs<T> *a, int n, cudaStream_t s)
+{
+    if (!a || n <= 0) return cudaErrorInvalidValue;
+#define C(P) rhs_group_dispatch<T, P>(a, n, s)
+    ADS_DISPATCH_P(p, C)
+#undef C
+}
+
+template <typename T>
+cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s)
+{
+    if (!a || n <= 0) return cudaErrorInvalidValue;
+#define C(P) col_group_dispatch<T, P>(a, maps, n, s)
+    ADS_DISPATCH_P(p, C)
+#undef C
+}
+
+}  // namespace ads

@@ -48,3 +48,16 @@ def test_invalid_arguments_rejected_on_host():
     with pytest.raises(ads.AdsError) as e:
         ads.Simulation((4, 0, 4), 2, 0.01, use_torch=False)
     assert e.value.code == -1
+
+
+def test_estimate_bytes_is_host_only_and_consistent():
+    from paper_1911_08158_gb300 import estimate_bytes
+    w32 = estimate_bytes((32, 40, 24), 2, "wave", "fp32")
+    w64 = estimate_bytes((32, 40, 24), 2, "wave", "fp64")
+    e32 = estimate_bytes((32, 40, 24), 2, "elastic", "fp32")
+    big = estimate_bytes((64, 40, 24), 2, "wave", "fp32")
+    assert 0 < w32 < w64 and w32 < e32 and w32 < big
+    # the four state arrays alone: (34 padded to 40) x 40 x 24 x 4 bytes each
+    assert w32 >= 4 * 40 * 40 * 24 * 4
+    assert estimate_bytes((32, 40, 24), 9, "wave", "fp32") == 0
+    assert estimate_bytes((0, 40, 24), 2, "wave", "fp32") == 0

@@ -1,0 +1,179 @@
+"""Grouped (batched) launches and the tile autotuner on the GPU.
+
+ads_batch_step advances many independent simulations with one grouped K1,
+K2 and K3 launch per step; the members share no data, so every result must
+equal what the simulation computes alone.  Parity with the oracle is
+checked for members of a mixed batch as well.
+"""
+import numpy as np
+import pytest
+
+from paper_1911_08158_gb300 import workloads as wl
+from tests.cases import assert_parity, check_state, oracle_wave
+
+pytestmark = pytest.mark.gpu
+
+
+def _make(case, precision, **kw):
+    from paper_1911_08158_gb300 import Simulation
+    sim = Simulation(case.n_elem, case.p, case.tau, c2=case.c2, precision=precision, **kw)
+    if case.source:
+        sim.set_source(case.source)
+    sim.set_gaussian_state(case.u0, None)
+    return sim
+
+
+def _mixed_cases():
+    """Uneven grids (ragged tails, one z-plane larger than the fused
+    budget so K1 takes row tiles plus a y sweep), degrees 1..4, sources and
+    pulses."""
+    cases = []
+    shapes = [((9, 13, 7), 2), ((21, 10, 17), 3), ((12, 12, 30), 2), ((40, 9, 11), 3), ((8, 8, 8), 1),
+              ((15, 11, 9), 4), ((190, 180, 5), 2), ((33, 7, 14), 2)]
+    for i, (ne, p) in enumerate(shapes):
+        if i % 2:
+            c = wl.ricker_case(ne=ne, p=p, tau=2e-3 + 1e-4 * i, steps=0, seed=i, sigma=0.08)
+        else:
+            c = wl.pulse_case(ne=ne, p=p, tau=1e-2 - 5e-4 * i, steps=0)
+        cases.append(c)
+    return cases
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_equals_alone(precision):
+    """37 steps (one untimed first step, two captured 16-step graphs and a
+    remainder) alone with ads_step and together with ads_batch_step."""
+    from paper_1911_08158_gb300 import batch_step
+    cases = _mixed_cases()
+    steps = 37
+    alone = []
+    for c in cases:
+        s = _make(c, precision)
+        s.step(steps)
+        alone.append(s.get_state())
+        s.close()
+    sims = [_make(c, precision) for c in cases]
+    batch_step(sims, steps)
+    for c, s, ref in zip(cases, sims, alone):
+        got = s.get_state()
+        assert s.step_count == steps
+        for k, name in enumerate("uva"):
+            assert np.array_equal(got[k], ref[k]), "%s %s %s: batch differs from alone (max %.3e)" % (
+                precision, c.n_elem, name, np.abs(got[k] - ref[k]).max())
+
+
+def test_batch_members_match_oracle():
+    from paper_1911_08158_gb300 import batch_step
+    cases = _mixed_cases()[:4]
+    steps = 20
+    sims = [_make(c, "fp64") for c in cases]
+    batch_step(sims, steps)
+    for c, s in zip(cases, sims):
+        ref = oracle_wave(c, steps)[steps]
+        got = s.get_state()
+        for k, name in enumerate("uva"):
+            assert_parity(got[k], ref[k], 1e-11, "%s p=%d %s" % (c.n_elem, c.p, name))
+
+
+def test_batch_more_than_one_launch_per_group():
+    """40 members of one degree: two grouped launches per kernel (32 + 8)."""
+    from paper_1911_08158_gb300 import batch_step
+    rng = np.random.default_rng(7)
+    cases = []
+    for i in range(40):
+        ne = tuple(int(v) for v in rng.integers(4, 12, 3))
+        cases.append(wl.pulse_case(ne=ne, p=2, tau=float(rng.uniform(5e-3, 2e-2)), steps=0))
+    alone = []
+    for c in cases:
+        s = _make(c, "fp32")
+        s.step(5)
+        alone.append(s.get_state()[0])
+        s.close()
+    sims = [_make(c, "fp32") for c in cases]
+    batch_step(sims, 5)
+    for s, ref in zip(sims, alone):
+        assert np.array_equal(s.get_state()[0], ref)
+
+
+def test_batch_changing_membership_and_elastic_member():
+    """Members joining and leaving between calls (the serving pattern), with
+    an elasticity simulation in the batch: each ends where it ends alone."""
+    from paper_1911_08158_gb300 import Simulation, batch_step
+    cases = _mixed_cases()[:5]
+    plan = [(0, 3, 9), (1, 0, 12), (2, 5, 4), (3, 2, 20), (4, 1, 7)]   # (case, join call, steps)
+    el = wl.elastic_case(ne=(7, 8, 6), p=2, tau=5e-3, steps=0, seed=3, sigma=0.1)
+
+    def make_el():
+        e = Simulation(el.n_elem, el.p, el.tau, kind="elastic", lam=el.lam, mu=el.mu, rho=el.rho,
+                       precision="fp32")
+        e.set_gaussian_state(None, el.v0)
+        return e
+
+    alone = {}
+    for ci, _, n in plan:
+        s = _make(cases[ci], "fp32")
+        s.step(n)
+        alone[ci] = s.get_state()
+        s.close()
+    e = make_el()
+    e.step(6)
+    el_alone = e.get_state()
+    e.close()
+
+    live, left, done = {}, {}, {}
+    e = make_el()
+    e_left = 6
+    for call in range(40):
+        if call > max(j for _, j, _ in plan) and not live and not e_left:
+            break
+        for ci, join, n in plan:
+            if join == call:
+                live[ci] = _make(cases[ci], "fp32")
+                left[ci] = n
+        k = min([left[c] for c in live] + ([e_left] if e_left else []) + [3])
+        if not live and not e_left:
+            continue
+        members = list(live.values()) + ([e] if e_left else [])
+        batch_step(members, k)
+        if e_left:
+            e_left -= k
+        for ci in list(live):
+            left[ci] -= k
+            if left[ci] == 0:
+                done[ci] = live.pop(ci).get_state()
+    assert not live and e_left == 0
+    for ci, _, _ in plan:
+        for k in range(3):
+            assert np.array_equal(done[ci][k], alone[ci][k])
+    got = e.get_state()
+    for k in range(2):
+        assert np.array_equal(got[k], el_alone[k])
+
+
+def test_autotune_keeps_state_and_picks_a_candidate():
+    c = wl.ricker_case(ne=(40, 130, 20), p=2, tau=2e-3, steps=0, seed=1, sigma=0.05)
+    s = _make(c, "fp32")
+    s.step(3)
+    before = s.get_state()
+    rows = s.autotune(2)
+    my = 130 + 2 - 2
+    assert rows == my or rows in (8, 16, 32, 64)
+    after = s.get_state()
+    assert s.step_count == 3
+    for k in range(3):
+        assert np.array_equal(before[k], after[k])
+    s.step(7)
+    ref = oracle_wave(c, 10)[10]
+    check_state(s.get_state(), ref, "fp32", c.tau, 3e-5, "autotuned tile %d" % rows)
+    # the choice is cached for the shape
+    t = _make(c, "fp32")
+    assert t.autotune(2) == rows
+
+
+def test_batch_rejects_bad_arguments():
+    from paper_1911_08158_gb300 import AdsError, batch_step
+    s = _make(wl.pulse_case(ne=6, p=2, steps=0), "fp32")
+    with pytest.raises(AdsError):
+        batch_step([s, s], 1)
+    with pytest.raises(AdsError):
+        batch_step([s], -1)
