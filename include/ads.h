@@ -94,6 +94,12 @@ typedef struct {
     void *alloc_ctx;      /* passed to alloc/free */
     int tile_lines;       /* y rows per CTA of the RHS + x-sweep kernel (a
                              tile of one z-plane); 0 = library choice */
+    int residual_correction; /* scalar wave, ADS_FP32 only: after the FP32
+                             sweeps give a, form the residual
+                             r = F - K p - G~ a in FP64 from the FP32 state,
+                             solve G~ d = r with the FP32 sweeps and take
+                             a + d (one step of iterative refinement); the
+                             update then uses the corrected a.  0 = off */
 } ads_options_t;
 
 /* Gaussian g(x) = amp * exp(-|x - center|^2 / den); for elasticity the

@@ -46,7 +46,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
-                ("tile_lines", ctypes.c_int)]
+                ("tile_lines", ctypes.c_int), ("residual_correction", ctypes.c_int)]
 
 
 class Gaussian(ctypes.Structure):
@@ -175,7 +175,8 @@ class Simulation:
 
     def __init__(self, n_elem, p: int, tau: float, kind: str = "wave", c2: float = 1.0, lam: float = 1.0,
                  mu: float = 1.0, rho: float = 1.0, length=(1.0, 1.0, 1.0), precision: str = "fp64",
-                 device: int = 0, use_torch: bool = True, stream=None, tile_lines: int = 0):
+                 device: int = 0, use_torch: bool = True, stream=None, tile_lines: int = 0,
+                 residual_correction: bool = False):
         L = library()
         ne = tuple(int(v) for v in (n_elem if np.ndim(n_elem) else (n_elem,) * 3))
         ln = tuple(float(v) for v in (length if np.ndim(length) else (length,) * 3))
@@ -192,9 +193,10 @@ class Simulation:
             self.stream = stream if stream is not None else torch.cuda.Stream(device)
             st = int(self.stream.cuda_stream)
             self._alloc = _TorchAllocator(device, st)
-            opts = Options(prec, device, st, self._alloc.alloc, self._alloc.free, None, tile_lines)
+            opts = Options(prec, device, st, self._alloc.alloc, self._alloc.free, None, tile_lines,
+                           int(residual_correction))
         else:
-            opts = Options(prec, device, None, ALLOC_FN(), FREE_FN(), None, tile_lines)
+            opts = Options(prec, device, None, ALLOC_FN(), FREE_FN(), None, tile_lines, int(residual_correction))
         h = ctypes.c_void_p()
         _check(L.ads_create(ctypes.byref(self._grid), int(p), float(tau), ctypes.byref(self._mat),
                             ctypes.byref(opts), ctypes.byref(h)))

@@ -100,6 +100,9 @@ struct ads_sim {
     unsigned long long uid = 0, version = 0;
     ads::ColMaps upd_maps{};   // TMA maps of P, Q for the z epilogue (scalar wave)
     bool has_maps = false;
+    // FP64 residual correction of the FP32 scalar-wave step (option)
+    bool refine = false;
+    void *R64 = nullptr, *P64 = nullptr, *A64 = nullptr, *T64 = nullptr;
 };
 
 namespace {
@@ -576,10 +579,48 @@ PwaveLaunch<T> pwave_launch(const ads_sim *s, bool write_a)
     return L;
 }
 
+// FP32 step with one FP64 residual correction (iterative refinement):
+//   a  = G~^{-1} R          FP32 sweeps (K1, K2, z sweep without update)
+//   r  = F - c2 K p - G~ a  in FP64 from the FP32 state p
+//   a += G~^{-1} r          FP32 sweeps of the residual
+// then the Newmark update of (p, q) with the corrected a.
+int pwave_refine_step(ads_sim *s, bool write_a, KernelTimer *kt)
+{
+    const PwaveLaunch<float> L = pwave_launch<float>(s, write_a);
+    const long long n = s->d.count();
+    float *X = (float *)s->X;
+    double *R = (double *)s->R64, *P64 = (double *)s->P64, *A64 = (double *)s->A64, *T = (double *)s->T64;
+    int rc;
+    if (kt && (rc = kt->mark(s->stream, L.fused ? "rhs_xy_sweep" : "rhs_x_sweep"))) return rc;
+    ADS_CK(ads::launch_rhs_group<float>(s->p, &L.rhs, 1, s->stream));
+    if (kt && (rc = kt->mark(s->stream, "yz_sweeps"))) return rc;
+    if ((rc = sweeps_yz<float>(s, X, SET_SPLIT, L.fused))) return rc;
+    if (kt && (rc = kt->mark(s->stream, "residual_fp64"))) return rc;
+    ADS_CK(ads::launch_convert<float>((const float *)s->P, P64, n, s->stream));
+    ADS_CK(ads::launch_convert<float>(X, A64, n, s->stream));
+    // R = F(t_{n+1}) - c2 K p: K1 in FP64 with identity factors
+    ads::RhsArgs<double> r = rhs_args<double>(s, P64, R, SET_IDENT, 1, true);
+    ADS_CK(ads::launch_rhs_group<double>(s->p, &r, 1, s->stream));
+    if ((rc = apply_kron64(s, s->t64.gband, A64, T, P64))) return rc;
+    ADS_CK(ads::launch_axpby(-1.0, T, 1.0, R, n, s->stream));
+    if (kt && (rc = kt->mark(s->stream, "correction_sweeps"))) return rc;
+    ADS_CK(ads::launch_convert_from<float>(R, X, n, s->stream));
+    ADS_CK(ads::launch_solve_x<float>(s->p, (const float *)s->t32.line[SET_SPLIT][0].base, X, s->d, s->stream));
+    if ((rc = sweeps_yz<float>(s, X, SET_SPLIT, false))) return rc;
+    ADS_CK(ads::launch_add_converted<float>(X, A64, n, s->stream));
+    ADS_CK(ads::launch_convert_from<float>(A64, X, n, s->stream));
+    if (kt && (rc = kt->mark(s->stream, "update"))) return rc;
+    ADS_CK(ads::launch_pq_update<float>((float *)s->P, (float *)s->Q, (float *)s->A, X, n,
+                                        (float)(s->tau * s->tau), write_a ? 1 : 0, s->d_step, s->stream));
+    if (kt && (rc = kt->mark(s->stream, ""))) return rc;
+    return ADS_OK;
+}
+
 // One scalar-wave step of one simulation (a group of one).
 template <typename T>
 int pwave_step(ads_sim *s, bool write_a, KernelTimer *kt = nullptr)
 {
+    if (sizeof(T) == 4 && s->refine) return pwave_refine_step(s, write_a, kt);
     const PwaveLaunch<T> L = pwave_launch<T>(s, write_a);
     int rc;
     if (kt && (rc = kt->mark(s->stream, L.fused ? "rhs_xy_sweep" : "rhs_x_sweep"))) return rc;
@@ -1229,6 +1270,7 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     s->alloc = o.alloc;
     s->dfree = o.free;
     s->actx = o.alloc_ctx;
+    s->refine = o.residual_correction != 0 && mat->kind == ADS_SCALAR_WAVE && o.precision == ADS_FP32;
     int dev = o.device;
     if (dev < 0) {
         if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -1285,6 +1327,14 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
         s->A = dalloc(s, n);
         s->X = dalloc(s, n);
         ok = ok && s->P && s->Q && s->A && s->X;
+        if (ok && s->refine) {
+            const size_t n64 = (size_t)s->d.count() * sizeof(double);
+            s->R64 = dalloc(s, n64);
+            s->P64 = dalloc(s, n64);
+            s->A64 = dalloc(s, n64);
+            s->T64 = dalloc(s, n64);
+            ok = s->R64 && s->P64 && s->A64 && s->T64;
+        }
     } else {
         s->U = dalloc(s, 3 * n);
         s->Up = dalloc(s, 3 * n);
@@ -1551,11 +1601,12 @@ int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps)
     }
     cudaSetDevice(sims[0]->device);
     // scalar-wave simulations share grouped launches per (precision, degree);
-    // elasticity advances on each simulation's own stream meanwhile
+    // elasticity (and the residual-corrected FP32 step) advances on each
+    // simulation's own stream meanwhile
     std::map<std::pair<int, int>, std::vector<ads_sim *>> groups;
     for (int i = 0; i < count; ++i) {
         ads_sim *s = sims[i];
-        if (s->kind == ADS_SCALAR_WAVE) {
+        if (s->kind == ADS_SCALAR_WAVE && !s->refine) {
             groups[{s->prec, s->p}].push_back(s);
         } else {
             int rc = ads_step(s, nsteps);

@@ -245,6 +245,26 @@ __global__ void k_atm_update(T *U, T *Up, const T *d, long long n, long long *st
 }
 
 template <typename T>
+__global__ void k_pq_update(T *P, T *Q, T *A, const T *x, long long n, T tau2, int write_a, long long *step)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && step) step[0] += 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T a = x[i];
+        const T q = Q[i] + tau2 * a;
+        Q[i] = q;
+        P[i] += q;
+        if (write_a) A[i] = a;
+    }
+}
+
+template <typename T>
+__global__ void k_add_converted(const T *x, double *y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += (double)x[i];
+}
+
+template <typename T>
 __global__ void k_add_source(T *out, Dims d, const T *fx, const T *fy, const T *fz, double scale, double freq,
                              double t0, const long long *step, int toff, double tau)
 {
@@ -493,6 +513,23 @@ cudaError_t launch_atm_update(T *U, T *Up, const T *d, long long n, long long *s
 }
 
 template <typename T>
+cudaError_t launch_pq_update(T *P, T *Q, T *A, const T *x, long long n, T tau2, int write_a, long long *step,
+                             cudaStream_t s)
+{
+    ++g_launches;
+    k_pq_update<T><<<grid_for(n, 256), 256, 0, s>>>(P, Q, A, x, n, tau2, write_a, step);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_add_converted(const T *x, double *y, long long n, cudaStream_t s)
+{
+    ++g_launches;
+    k_add_converted<T><<<grid_for(n, 256), 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_add_source(T *out, Dims d, const T *fx, const T *fy, const T *fz, double scale, double freq,
                               double t0, const long long *step, int toff, double tau, cudaStream_t s)
 {
@@ -524,6 +561,8 @@ cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long 
     template cudaError_t launch_convert_from<T>(const double *, T *, long long, cudaStream_t);                      \
     template cudaError_t launch_lincomb<T>(T *, T, const T *, T, const T *, long long, cudaStream_t);              \
     template cudaError_t launch_atm_update<T>(T *, T *, const T *, long long, long long *, cudaStream_t);          \
+    template cudaError_t launch_pq_update<T>(T *, T *, T *, const T *, long long, T, int, long long *, cudaStream_t); \
+    template cudaError_t launch_add_converted<T>(const T *, double *, long long, cudaStream_t);                     \
     template cudaError_t launch_add_source<T>(T *, Dims, const T *, const T *, const T *, double, double, double,   \
                                               const long long *, int, double, cudaStream_t);                       \
     template cudaError_t launch_el_to_uv<T>(const T *, const T *, double *, double *, long long, double, cudaStream_t);

@@ -181,6 +181,14 @@ cudaError_t launch_dot(const double *x, const double *y, long long n, double *pa
 // out = a*x + b*y over n elements (y may be null)
 template <typename T>
 cudaError_t launch_lincomb(T *out, T a, const T *x, T b, const T *y, long long n, cudaStream_t s);
+// Newmark update of the (p, q) state from a solved acceleration x:
+//   q += tau2 x;  p += q;  a = x (if write_a);  step[0] += 1
+template <typename T>
+cudaError_t launch_pq_update(T *P, T *Q, T *A, const T *x, long long n, T tau2, int write_a, long long *step,
+                             cudaStream_t s);
+// y += (double) x  over n elements
+template <typename T>
+cudaError_t launch_add_converted(const T *x, double *y, long long n, cudaStream_t s);
 // three-level update (elasticity): t = U; U = 2U - Up + d; Up = t; step[0] += 1
 template <typename T>
 cudaError_t launch_atm_update(T *U, T *Up, const T *d, long long n, long long *step, cudaStream_t s);
