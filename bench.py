@@ -221,6 +221,12 @@ def run_ours(args):
                 "peak_source": "measured" if peaks else "fallback",
                 "kernel_share": {k: round(v / sum(tot.values()), 4) for k, v in tot.items()},
                 "kernel_ms": {k: round(v, 5) for k, v in tot.items()}}
+    # the whole step: K1 reads p and writes x (8 B), K3 reads x, p, q and
+    # writes p, q (20 B) per interior DOF; a is stored once per 16 steps
+    interior = sum((s.n[0] - 2) * (s.n[1] - 2) * (s.n[2] - 2) for s in sims)
+    step_gbs = interior * NSTEPS * args.steps * (28 + 4 / 16) / t_dev / 1e9
+    roofline["step"] = {"bytes_per_interior_dof": 28.25, "achieved": round(step_gbs, 1),
+                        "frac": round(step_gbs / peak, 4)}
 
     # ---- accuracy of the FP32 path against the FP64 path (fresh runs)
     acc = {}
@@ -408,24 +414,29 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def profile_case(ne, p: int, steps: int):
-    """Small fixed case for ncu captures: one FP32 simulation with ne
-    (n or nx,ny,nz) elements (no timing), a few steps via the profiling entry."""
+def profile_case(ne, p: int, steps: int, batch: int = 1):
+    """Small fixed case for ncu captures: `batch` FP32 simulations of ne
+    (n or nx,ny,nz) elements advanced together (grouped launches; no
+    timing): two warm-up steps, then `steps` single steps."""
     import torch
 
     import paper_1911_08158_gb300 as ads
     from paper_1911_08158_gb300 import workloads as wl
 
     torch.cuda.set_device(0)
-    case = wl.ricker_case(ne=ne, p=p)
-    sim = ads.Simulation(case.n_elem, case.p, case.tau, precision="fp32")
-    sim.set_source(case.source)
-    sim.set_gaussian_state(None, None)
-    sim.step(2)                      # graph path, as in the benchmark
+    sims = []
+    for i in range(batch):
+        case = wl.ricker_case(ne=ne, p=p, seed=i)
+        sim = ads.Simulation(case.n_elem, case.p, case.tau, precision="fp32")
+        sim.set_source(case.source)
+        sim.set_gaussian_state(None, None)
+        sims.append(sim)
+    ads.batch_step(sims, 2)
     for _ in range(steps):
-        sim.profile_step()
+        ads.batch_step(sims, 1)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": ne, "p": p, "steps": steps, "device_bytes": sim.device_bytes}))
+    print(json.dumps({"profile_case": ne, "p": p, "steps": steps, "batch": batch,
+                      "device_bytes": sum(s.device_bytes for s in sims)}))
 
 
 def main():
@@ -441,10 +452,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=500)
     ap.add_argument("--profile-case", default="", help="run a small case (n or nx,ny,nz elements) for ncu and exit")
     ap.add_argument("--profile-p", type=int, default=2)
+    ap.add_argument("--profile-batch", type=int, default=1, help="simulations advanced together in the profile case")
     args = ap.parse_args()
     if args.profile_case:
         ne = tuple(int(v) for v in args.profile_case.split(","))
-        profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4)
+        profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4, args.profile_batch)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -243,8 +243,10 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
 
 /* Measurement: run ONE time step with CUDA events recorded on the
  * simulation's stream between its kernels; fills names[i] (static strings)
- * and ms[i] (device time of kernel i) for i < min(cap, *count).  Advances the
- * state like ads_step(sim, 1).  Waits. */
+ * and ms[i] (device time of kernel i) for i < min(cap, *count).  The stream
+ * is held by a 2 ms device-side sleep while the step is queued, so the
+ * intervals hold no host launch latency.  Advances the state like
+ * ads_step(sim, 1).  Waits. */
 int ads_profile_step(ads_sim_t *sim, const char **names, float *ms, int cap, int *count);
 
 /* Kernel launches issued by this library since load (all simulations). */

@@ -1849,6 +1849,9 @@ int ads_profile_step(ads_sim_t *s, const char **names, float *ms, int cap, int *
     cudaSetDevice(s->device);
     KernelTimer kt;
     int rc;
+    // the stream sleeps while the step and its events are queued, so every
+    // interval measures device time only, not the host's launch latency
+    ADS_CK(ads::launch_delay(2000000ull, s->stream));
     if (s->kind == ADS_ELASTIC)
         rc = s->prec == ADS_FP64 ? elastic_step<double>(s, &kt) : elastic_step<float>(s, &kt);
     else

@@ -244,6 +244,17 @@ __global__ void k_atm_update(T *U, T *Up, const T *d, long long n, long long *st
     }
 }
 
+__global__ void k_delay(unsigned long long ns)
+{
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    t = t0;
+    while (t - t0 < ns) {
+        __nanosleep(1000);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    }
+}
+
 template <typename T>
 __global__ void k_pq_update(T *P, T *Q, T *A, const T *x, long long n, T tau2, int write_a, long long *step)
 {
@@ -509,6 +520,12 @@ cudaError_t launch_atm_update(T *U, T *Up, const T *d, long long n, long long *s
 {
     ++g_launches;
     k_atm_update<T><<<grid_for(n, 256), 256, 0, s>>>(U, Up, d, n, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_delay(unsigned long long ns, cudaStream_t s)
+{
+    k_delay<<<1, 1, 0, s>>>(ns);
     return cudaGetLastError();
 }
 

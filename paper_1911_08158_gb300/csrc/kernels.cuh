@@ -200,6 +200,10 @@ cudaError_t launch_add_source(T *out, Dims d, const T *fx, const T *fy, const T 
 template <typename T>
 cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long long n, double tau, cudaStream_t s);
 
+// one thread sleeps for `ns` nanoseconds of the global timer (keeps the
+// stream busy while the host queues the launches that follow)
+cudaError_t launch_delay(unsigned long long ns, cudaStream_t s);
+
 extern unsigned long long g_launches;
 
 }  // namespace ads

@@ -342,15 +342,17 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
 // ---------------------------------------------------------------- K1
 //
 // One CTA per (z-plane, y-tile of ty rows).  Shared memory: S1, S2 [ty][RS]
-// (RS odd), carry buffers and the 1D tables.  Phases:
-//  1. z- then y-contraction of p, thread per x, streaming along y with a
-//     register window (loads prefetched two rows ahead):
+// (RS odd), carry buffers and the 1D tables (one bulk copy, waited for
+// after phase 1).  Phases:
+//  1. z- then y-contraction of p, thread per (column pair, row chunk),
+//     streaming along y with a register ring (y bands from global memory):
 //        s1 = (My.Mz) p,   s2 = (Ky.Mz + My.Kz) p       (K p = Kx s1 + Mx s2)
 //  2. x-direction, thread per (row, segment of SEG): R = F - c2 (Kx s1 + Mx s2)
 //     is formed in registers while the local forward pass runs, then the
 //     carry exchange and passes 2-3; the row is written back to S1.
-//  3. whole plane in the tile: y-direction solve, thread per (x, segment).
-//  4. coalesced store.
+//  3. whole plane in the tile: y-direction solve, thread per (x, segment),
+//     results stored from registers to global memory.
+//  4. row tiles only: coalesced store of S1.
 template <typename T>
 struct RhsThreads {
     static constexpr int value = sizeof(T) == 8 ? 256 : 512;   // FP64: more registers per thread
@@ -422,11 +424,11 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
         }
         s_r = r;
     }
-    __syncthreads();
-    if (!mbar_wait_bounded(&bar, 0, a.err)) return;   // error recorded for the host
+    __syncthreads();   // barrier initialised, s_r set
 
-    // ---- phase 1
+    // ---- phase 1 (overlaps the table copy: its y bands are read from global memory)
     {
+        const T *gMy = a.bandM[1].v, *gKy = a.bandK[1].v;
         T cm[W], ck[W], mym[W], myk[W];
         const int ylo = a.bandM[1].lo, yhi = a.bandM[1].hi;   // K shares M's interior range
         bool zok[W];
@@ -435,37 +437,44 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
             cm[k] = a.bandM[2].v[z * W + k];
             ck[k] = a.bandK[2].v[z * W + k];
             const int mid = ylo < yhi ? ylo : 0;
-            mym[k] = bMy[mid * W + k];
-            myk[k] = bKy[mid * W + k];
+            mym[k] = gMy[mid * W + k];
+            myk[k] = gKy[mid * W + k];
             zok[k] = (z + k - P >= 0) && (z + k - P < mz);
         }
+        // work items (column pair, row chunk) spread over all lanes of the
+        // CTA: as many chunks as keep every lane busy, whatever mx is
         const int npair = (mx + 1) >> 1;          // column pairs (the last may end in padding)
-        const int XG = (npair + 31) >> 5;
-        int YC = nwarps / XG;
+        int YC = NT / npair;
         if (YC < 1) YC = 1;
+        if (YC > tye) YC = tye;
         const int rows_per = (tye + YC - 1) / YC;
         const bool zin = z >= P && z + P < mz;
-        for (int item = warp; item < XG * YC; item += nwarps) {
-            const int xg = item % XG, yc = item / XG;
-            const int pr = xg * 32 + lane;
+        for (int item = tid; item < npair * YC; item += NT) {
+            const int pr = item % npair, yc = item / npair;
             const int x = 2 * pr;
             const int yb = y0 + yc * rows_per;
             int ye = yb + rows_per;
             if (ye > y0 + tye) ye = y0 + tye;
-            if (yb >= ye || pr >= npair) continue;
+            const bool live = yb < ye;
+            const bool guard = live && (!zin || yb - P < 0 || ye + P > my);
+            const bool inter = !live || (yb >= ylo && ye <= yhi);
+            // one variant per warp (lanes of two row chunks may share a warp)
+            const unsigned am = __activemask();
+            const bool wguard = __any_sync(am, guard), winter = __all_sync(am, inter);
+            if (!live) continue;
             const T *col0 = a.in + x + (long long)(z - P) * plane;   // plane z-P, row 0, column x
             T *c1 = S1 + x - (size_t)y0 * RS, *c2 = S2 + x - (size_t)y0 * RS;
-            const bool guard = !zin || yb - P < 0 || ye + P > my;
-            const bool inter = yb >= ylo && ye <= yhi;
-            if (!guard && inter)
-                phase1_chunk<T, P, false, true>(col0, plane, sx, my, zok, cm, ck, mym, myk, bMy, bKy, ylo, yhi, yb, ye, c1, c2, RS);
-            else if (!guard)
-                phase1_chunk<T, P, false, false>(col0, plane, sx, my, zok, cm, ck, mym, myk, bMy, bKy, ylo, yhi, yb, ye, c1, c2, RS);
+            if (!wguard && winter)
+                phase1_chunk<T, P, false, true>(col0, plane, sx, my, zok, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
+            else if (!wguard)
+                phase1_chunk<T, P, false, false>(col0, plane, sx, my, zok, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
             else
-                phase1_chunk<T, P, true, false>(col0, plane, sx, my, zok, cm, ck, mym, myk, bMy, bKy, ylo, yhi, yb, ye, c1, c2, RS);
+                phase1_chunk<T, P, true, false>(col0, plane, sx, my, zok, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
         }
     }
-    __syncthreads();
+    // tables in shared memory from here on; every thread leaves together if
+    // the copy did not arrive (the error word tells the host)
+    if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, a.err))) return;
 
     // ---- phase 2: x-direction, thread per (row, segment); rounds of row groups
     const int RG = rows_pad >> 5;
@@ -534,17 +543,20 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
             for (int k = 0; k < SEG; ++k) v[k] = (k < n) ? S1[(size_t)(b0 + k) * RS + x] : T(0);
             if (on) seg_pass1<T, P, SEG>(LY.fac + b0 * W, v);
             seg_finish<T, P, SEG>(LY, on, s, x, cld, CT, CH, v);
+            // finished columns go straight to global memory (lanes = consecutive
+            // x: one coalesced row segment per k); the next round reads other
+            // columns of S1 and its carry writes follow seg_finish's barriers
             if (on) {
+                T *dst = a.out + (long long)z * plane + (long long)b0 * sx + x;
 #pragma unroll
                 for (int k = 0; k < SEG; ++k)
-                    if (k < n) S1[(size_t)(b0 + k) * RS + x] = v[k];
+                    if (k < n) dst[(long long)k * sx] = v[k];
             }
-            __syncthreads();
         }
     }
 
-    // ---- phase 4: store
-    {
+    // ---- phase 4: store (row tiles; the fused path stored in phase 3)
+    if (!fuse_y) {
         T *dst0 = a.out + (long long)z * plane + (long long)y0 * sx;
         for (int l = warp; l < tye; l += nwarps) {
             const T *src = S1 + (size_t)l * RS;
@@ -630,7 +642,7 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
     for (int k = 0; k < SEG; ++k) v[k] = (k < n) ? in[(long long)k * stride] : T(0);
     const LineSm<T> L = line_carve<T, P>(lb, a.ln.S * SEG, a.ln.S);
     __syncthreads();   // barriers initialised
-    if (!mbar_wait_bounded(&bar_tab, 0, a.err)) return;
+    if (!__syncthreads_and(mbar_wait_bounded(&bar_tab, 0, a.err))) return;
     if (on) seg_pass1<T, P, SEG>(L.fac + b0 * (2 * P + 1), v);
     seg_finish<T, P, SEG>(L, on, s, lane, 32, CT, CH, v);
     const long long off = base + x + (long long)b0 * stride;
@@ -642,7 +654,7 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
             if (k < n) out[(long long)k * stride] = v[k];
         return;
     }
-    if (!mbar_wait_bounded(&bar, 0, a.err)) return;   // error recorded for the host
+    if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, a.err))) return;   // error recorded for the host
     if (on) {
         const T tau2 = a.tau2;
 #pragma unroll
