@@ -199,7 +199,7 @@ int ads_get_step(const ads_sim_t *sim, long long *n);
  * exactly conserved invariant when f = 0).  Elasticity: kinetic
  * 1/2 rho V^T M V with V = (U^n - U^{n-1})/tau, potential 1/2 U^T Ups U,
  * kin_mod = the conserved invariant of the three-level scheme at n-1/2
- * (Sec. 6).  Reductions in FP64 with compensated summation.  Any output
+ * (Sec. 5.1, eq. equality).  Reductions in FP64 with compensated summation.  Any output
  * may be NULL.  Waits for the stream. */
 int ads_energy(ads_sim_t *sim, double *kinetic, double *potential, double *kin_mod);
 
@@ -251,6 +251,15 @@ int ads_profile_step(ads_sim_t *sim, const char **names, float *ms, int cap, int
 
 /* Kernel launches issued by this library since load (all simulations). */
 long long ads_launch_count(void);
+
+/* Self-test of the device-side timeout path: one CTA waits on an mbarrier
+ * whose transaction bytes never arrive (no copy is issued) for at most
+ * `cycles` SM cycles (1 .. 4e9); the wait runs out, the kernel records the
+ * timeout in a device error word and returns, as every bounded wait of the
+ * library does.  Returns ADS_ERR_TIMEOUT when that happened (the expected
+ * outcome), ADS_OK if the wait completed, ADS_ERR_CUDA on a launch error.
+ * The CUDA context stays usable.  device < 0: the current device.  Waits. */
+int ads_selftest_timeout(int device, long long cycles);
 
 const char *ads_last_error(void);
 

@@ -87,6 +87,7 @@ def library() -> ctypes.CDLL:
         L.ads_autotune.argtypes = [vp, i, ctypes.POINTER(i)]
         L.ads_estimate_bytes.argtypes = [ctypes.POINTER(Grid), i, i, i]
         L.ads_estimate_bytes.restype = sz
+        L.ads_selftest_timeout.argtypes = [i, ctypes.c_longlong]
         L.ads_sync.argtypes = [vp]
         L.ads_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.ads_energy.argtypes = [vp, _D, _D, _D]
@@ -343,6 +344,12 @@ class Simulation:
         rows = ctypes.c_int(0)
         _check(library().ads_autotune(self._h, int(trial_steps), ctypes.byref(rows)))
         return rows.value
+
+
+def selftest_timeout(device: int = 0, cycles: int = 20_000_000) -> int:
+    """Run the bounded-wait self-test (ads_selftest_timeout); returns its code
+    (ADS_ERR_TIMEOUT = -4 is the expected outcome)."""
+    return int(library().ads_selftest_timeout(int(device), int(cycles)))
 
 
 def estimate_bytes(n_elem, p: int, kind: str = "wave", precision: str = "fp32") -> int:

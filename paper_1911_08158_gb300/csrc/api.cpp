@@ -1616,6 +1616,24 @@ int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps)
     return batch_groups(groups, nsteps);
 }
 
+int ads_selftest_timeout(int device, long long cycles)
+{
+    if (cycles < 1 || cycles > 4000000000LL) return fail(ADS_ERR_INVALID_ARG, "ads_selftest_timeout: cycles");
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) return fail(ADS_ERR_CUDA, "no CUDA device");
+    ADS_CK(cudaSetDevice(device));
+    int *err = nullptr;
+    ADS_CK(cudaMalloc(&err, 2 * sizeof(int)));
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemset(err, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = ads::launch_wait_selftest(cycles, err, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, err, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return fail(ADS_ERR_CUDA, std::string("ads_selftest_timeout: ") + cudaGetErrorString(e));
+    if (h[0] == ads::kDevErrTimeout) return fail(ADS_ERR_TIMEOUT, "self-test: the bounded device wait ran out");
+    return ADS_OK;
+}
+
 int ads_autotune(ads_sim_t *s, int trial_steps, int *tile_rows)
 {
     if (!s || trial_steps < 0) return fail(ADS_ERR_INVALID_ARG, "ads_autotune: bad arguments");

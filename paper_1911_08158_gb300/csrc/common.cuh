@@ -4,7 +4,8 @@
 
 namespace ads {
 
-// Ricker wavelet r(t) = (1 - 2 a) exp(-a), a = (pi f (t - t0))^2  (Sec. 5 source)
+// Ricker wavelet r(t) = (1 - 2 a) exp(-a), a = (pi f (t - t0))^2: time profile of the
+// source term F_{n+1} = (f(t_{n+1}), w) of Sec. 2
 __device__ __forceinline__ double ricker_dev(double f, double t0, double t)
 {
     const double pi = 3.141592653589793238462643;

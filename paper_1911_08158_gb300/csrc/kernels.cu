@@ -11,6 +11,7 @@
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace ads {
 
@@ -242,6 +243,21 @@ __global__ void k_atm_update(T *U, T *Up, const T *d, long long n, long long *st
         U[i] = T(2) * u - Up[i] + d[i];
         Up[i] = u;
     }
+}
+
+// One CTA waits on an mbarrier whose transaction bytes never arrive (no
+// copy is issued): the bounded wait must run out and record the timeout.
+__global__ void k_wait_selftest(long long cycles, int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(&bar, 16);
+    }
+    __syncthreads();
+    if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, err, cycles))) return;
+    if (threadIdx.x == 0) atomicExch(err + 1, 1);   // the wait completed (not expected)
 }
 
 __global__ void k_delay(unsigned long long ns)
@@ -520,6 +536,12 @@ cudaError_t launch_atm_update(T *U, T *Up, const T *d, long long n, long long *s
 {
     ++g_launches;
     k_atm_update<T><<<grid_for(n, 256), 256, 0, s>>>(U, Up, d, n, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(long long cycles, int *err, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 64, 0, s>>>(cycles, err);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,9 @@
 
 namespace ads {
 
+// device error codes written to a simulation's error word by bounded waits
+enum { kDevErrTimeout = 1, kDevErrAlign = 2 };
+
 constexpr int kSeg = 32;     // rows per register segment of the line solves
 constexpr int kBatch = 32;   // simulations per grouped launch
 
@@ -203,6 +206,8 @@ cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long 
 // one thread sleeps for `ns` nanoseconds of the global timer (keeps the
 // stream busy while the host queues the launches that follow)
 cudaError_t launch_delay(unsigned long long ns, cudaStream_t s);
+// bounded-wait self-test: err[0] = timeout code if the wait ran out, err[1] = 1 if it completed
+cudaError_t launch_wait_selftest(long long cycles, int *err, cudaStream_t s);
 
 extern unsigned long long g_launches;
 

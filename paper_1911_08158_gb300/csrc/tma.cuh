@@ -4,10 +4,9 @@
 #include <cuda.h>
 #include <stdint.h>
 
-namespace ads {
+#include "kernels.cuh"   // device error codes
 
-// device error codes written to the simulation's error word
-enum { kDevErrTimeout = 1, kDevErrAlign = 2 };
+namespace ads {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

@@ -1,4 +1,4 @@
-"""Seeded synthetic workloads shaped like the paper's runs (Sec. 4 and 7:
+"""Seeded synthetic workloads shaped like the paper's runs (Sec. 4 and 6:
 32^3 elements, tau = 0.01) at the sizes of the benchmark configurations.
 
 Input generation only: grid sizes, degrees, time steps, Gaussian centres and

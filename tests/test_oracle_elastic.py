@@ -1,10 +1,10 @@
-"""Pins of the oracle's linear-elasticity path (Sec. 5-7).
+"""Pins of the oracle's linear-elasticity path (Sec. 5-6).
 
 Upsilon is checked against a brute-force 3D quadrature of the bilinear form
 2 mu e(w):e(u) + lam div w div u (independent of the Kronecker block
 formulas); the alternating-triangular step against a dense block-triangular
 solve built on that brute-force matrix; the scheme against its exactly
-conserved discrete invariant (a priori estimate of Sec. 6), the stability
+conserved discrete invariant (a priori estimate of Sec. 5.1, eq. equality), the stability
 condition D - tau^2 Ups / 4 > 0, boundedness for large tau and second order."""
 import numpy as np
 import pytest
