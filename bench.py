@@ -17,6 +17,7 @@ step; inputs stay resident in HBM.
   fp64   : the FP64 path on the same workload (the path the FP32 one beats)
   roofline: dominant kernel, algorithmic bytes / its CUDA-event time
   cpu_baseline: the FP64 CPU oracle on a bounded sample of the workload
+  elastic: the 96^3 elasticity configuration (p = 2, 100 steps), FP32 and FP64
   batch  : 64 uneven P-wave simulations (elements per axis U{32..160}, p in
            {2, 3}, tau in [1e-3, 5e-3], Gaussian pulses), 50 steps each, FP32,
            autotuned tiles, grouped launches replayed from CUDA graphs
@@ -295,6 +296,8 @@ def run_ours(args):
     }
     if not args.no_batch:
         out["batch"] = guarded(run_batch, args, stream, flush)
+    if not args.no_elastic:
+        out["elastic"] = guarded(run_elastic, args, stream, flush)
     if not args.no_serve:
         out["serving"] = guarded(run_serving, args)
     if rank == 0 and not args.no_cpu_baseline:
@@ -349,6 +352,42 @@ def run_batch(args, stream, flush):
             "total_dofs": n, "reps": reps, "ms_per_rep": t / reps * 1e3,
             "tiles_fused": sum(1 for s, r in zip(cases, tiles) if r == s.n_elem[1] + s.p - 2),
             "workload": "batch64_pwave_uneven_32to160_p2p3_50steps_fp32"}
+
+
+def run_elastic(args, stream, flush):
+    """Elasticity (96^3 elements, p = 2, lambda = mu = rho = 1, tau = 2e-3,
+    100 steps, seeded Gaussian velocity pulse): FP32 and FP64 paths, the
+    FP32 displacement error against the FP64 path, and per-phase times."""
+    import torch
+
+    import paper_1911_08158_gb300 as ads
+    from paper_1911_08158_gb300 import workloads as wl
+    case = wl.elastic_case()
+    out = {"workload": "elastic_96cubed_p2_100steps", "steps": case.steps}
+    finals = {}
+    for prec in ("fp32", "fp64"):
+        sim = ads.Simulation(case.n_elem, case.p, case.tau, kind="elastic", lam=case.lam, mu=case.mu,
+                             rho=case.rho, precision=prec, stream=stream)
+        sim.set_gaussian_state(None, case.v0)
+        sim.step(2)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(case.steps)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        dofs = int(np.prod(sim.n)) * 3
+        out[prec] = {"value": dofs * case.steps / t, "unit": UNIT, "ms_per_step": t / case.steps * 1e3}
+        finals[prec] = sim.get_state(fields=("u",))[0]
+        if prec == "fp32":
+            out["phases_ms"] = {k: round(v, 4) for k, v in sim.profile_step()}
+        sim.close()
+    out["rel_l2_fp32_vs_fp64_u"] = float(np.linalg.norm(finals["fp32"] - finals["fp64"]) /
+                                         np.linalg.norm(finals["fp64"]))
+    return out
 
 
 def run_serving(args):
@@ -449,6 +488,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-simulation batch measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-elastic", action="store_true", help="skip the elasticity measurement")
     ap.add_argument("--serve-requests", type=int, default=500)
     ap.add_argument("--profile-case", default="", help="run a small case (n or nx,ny,nz elements) for ncu and exit")
     ap.add_argument("--profile-p", type=int, default=2)

@@ -50,13 +50,17 @@ struct LineTables {
 };
 
 enum { SET_SPLIT = 0, SET_MASS = 1, SET_IDENT = 2, SET_ELAS0 = 3, SET_ELAS1 = 4, NSETS = 5 };
+// K1 table images: one per factor set (x and y tables of that set), plus the
+// three mixed images of the elastic diagonal blocks (component i: set ELAS0
+// on axis i, ELAS1 on the others)
+enum { IMG_EL = NSETS, NIMG = NSETS + 3 };
 
 // Device copy of a set of FP64 host tables in precision T.
 struct TableSet {
     void *M[3] = {}, *K[3] = {}, *B[3] = {};   // operator bands [m_pad][2p+1]
     LineTables line[NSETS][3];                 // per factor set and axis
-    void *img[NSETS] = {};                     // K1 images (x and y tables of a set)
-    int img_bytes[NSETS] = {};
+    void *img[NIMG] = {};                      // K1 images (x and y tables of a set)
+    int img_bytes[NIMG] = {};
     void *gband[3] = {};                       // bands of M + eta c2 K (energies)
     void *src[3] = {};                         // separable source load vectors
 };
@@ -220,11 +224,11 @@ int upload_padded(ads_sim *s, const std::vector<double> &h, void **dst, int *byt
     return ADS_OK;
 }
 
-// K1 image of factor set `set`: bMx bKx | bMy bKy | fx | fy | x tables | y tables
+// K1 image in slot `slot`: bMx bKx | bMy bKy | fx | fy | x tables of xset | y tables of yset
 template <typename T>
-int upload_rhs_image(ads_sim *s, TableSet &ts, int set)
+int upload_rhs_image(ads_sim *s, TableSet &ts, int slot, int xset, int yset)
 {
-    if (s->hline[set][0].empty()) return ADS_OK;
+    if (s->hline[xset][0].empty() || s->hline[yset][1].empty()) return ADS_OK;
     std::vector<double> img;
     auto add = [&](const std::vector<double> &v) { img.insert(img.end(), v.begin(), v.end()); };
     add(s->hM[0]);
@@ -236,13 +240,30 @@ int upload_rhs_image(ads_sim *s, TableSet &ts, int set)
         if (s->hsrc[a].size() == mp) add(s->hsrc[a]);
         else img.insert(img.end(), mp, 0.0);
     }
-    add(s->hline[set][0]);
-    add(s->hline[set][1]);
-    if (ts.img[set]) {
-        dfree(s, ts.img[set]);
-        ts.img[set] = nullptr;
+    add(s->hline[xset][0]);
+    add(s->hline[yset][1]);
+    if (ts.img[slot]) {
+        dfree(s, ts.img[slot]);
+        ts.img[slot] = nullptr;
     }
-    return upload_padded<T>(s, img, &ts.img[set], &ts.img_bytes[set]);
+    return upload_padded<T>(s, img, &ts.img[slot], &ts.img_bytes[slot]);
+}
+
+// every K1 image of a table set
+template <typename T>
+int upload_rhs_images(ads_sim *s, TableSet &ts)
+{
+    for (int set = 0; set < NSETS; ++set) {
+        int rc = upload_rhs_image<T>(s, ts, set, set, set);
+        if (rc) return rc;
+    }
+    if (s->kind == ADS_ELASTIC)
+        for (int i = 0; i < 3; ++i) {
+            int rc = upload_rhs_image<T>(s, ts, IMG_EL + i, i == 0 ? SET_ELAS0 : SET_ELAS1,
+                                         i == 1 ? SET_ELAS0 : SET_ELAS1);
+            if (rc) return rc;
+        }
+    return ADS_OK;
 }
 
 template <typename T>
@@ -297,11 +318,7 @@ int build_tables(ads_sim *s, TableSet &ts)
             if ((rc = upload<T>(s, g, &ts.gband[a]))) return rc;
         }
     }
-    for (int set = 0; set < NSETS; ++set) {
-        int rc = upload_rhs_image<T>(s, ts, set);
-        if (rc) return rc;
-    }
-    return ADS_OK;
+    return upload_rhs_images<T>(s, ts);
 }
 
 template <typename T>
@@ -675,10 +692,10 @@ int kron3(ads_sim *s, const T *in, T *out, const int *which, T coef, bool accumu
     const TableSet &ts = tables_for<T>(s);
     const void *band[3];
     for (int a = 0; a < 3; ++a) band[a] = which[a] == 0 ? ts.M[a] : (which[a] == 1 ? ts.K[a] : ts.B[a]);
-    ADS_CK(ads::launch_axis_apply<T>(s->p, (const T *)band[0], 0, in, ta, s->d, T(1), T(0), 0, s->stream));
-    ADS_CK(ads::launch_axis_apply<T>(s->p, (const T *)band[1], 1, ta, tb, s->d, T(1), T(0), 0, s->stream));
-    ADS_CK(ads::launch_axis_apply<T>(s->p, (const T *)band[2], 2, tb, out, s->d, coef, accumulate ? T(1) : T(0), 0,
-                                     s->stream));
+    (void)ta;
+    (void)tb;
+    ADS_CK(ads::launch_kron3<T>(s->p, (const T *)band[0], (const T *)band[1], (const T *)band[2], in, out, s->d, coef,
+                                accumulate ? T(1) : T(0), s->stream));
     return ADS_OK;
 }
 
@@ -710,22 +727,31 @@ int apply_upsilon(ads_sim *s, const T *U, T *out, T *ta, T *tb)
 }
 
 // data <- (x)_xi (M_xi + d_i,xi K_xi)^{-1} data, d = tau^2 c_i,xi / (4 rho),
-// c_i,xi = 2 mu + lam on axis i, mu otherwise (eq. spill)
+// c_i,xi = 2 mu + lam on axis i, mu otherwise (eq. spill): K1 in direct
+// mode (x, and y when the plane fits), then the y sweep if needed and the z
+// sweep
 template <typename T>
 int elastic_diag_solve(ads_sim *s, int i, T *data)
 {
     const TableSet &ts = tables_for<T>(s);
     auto set = [&](int a) { return a == i ? SET_ELAS0 : SET_ELAS1; };
-    ADS_CK(ads::launch_solve_x<T>(s->p, (const T *)ts.line[set(0)][0].base, data, s->d, s->stream));
+    ads::RhsArgs<T> r = rhs_args<T>(s, data, data, set(0), 0, false);
+    r.direct = 1;
+    r.ly = line_dev<T>(ts.line[set(1)][1]);
+    r.img = (const T *)ts.img[IMG_EL + i];
+    r.img_bytes = ts.img_bytes[IMG_EL + i];
+    ADS_CK(ads::launch_rhs_group<T>(s->p, &r, 1, s->stream));
     ads::ColArgs<T> c{};
     c.d = s->d;
     c.mode = 0;
     c.in = data;
     c.out = data;
     c.err = s->d_err;
-    c.axis = 1;
-    c.ln = line_dev<T>(ts.line[set(1)][1]);
-    ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    if (r.ty != s->d.my) {
+        c.axis = 1;
+        c.ln = line_dev<T>(ts.line[set(1)][1]);
+        ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    }
     c.axis = 2;
     c.ln = line_dev<T>(ts.line[set(2)][2]);
     ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
@@ -878,11 +904,9 @@ void drop_graphs(ads_sim *s)
 // drop captured graphs (they hold the old image pointers)
 int rebuild_images(ads_sim *s)
 {
-    for (int set = 0; set < NSETS; ++set) {
-        int rc = upload_rhs_image<double>(s, s->t64, set);
-        if (rc) return rc;
-        if (s->prec == ADS_FP32 && (rc = upload_rhs_image<float>(s, s->t32, set))) return rc;
-    }
+    int rc = upload_rhs_images<double>(s, s->t64);
+    if (rc) return rc;
+    if (s->prec == ADS_FP32 && (rc = upload_rhs_images<float>(s, s->t32))) return rc;
     drop_graphs(s);
     return ADS_OK;
 }
@@ -1810,7 +1834,8 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
             add(mp[a] * W * e);                                             // bands of M + eta K
             add(mp[a] * e);                                                 // source load vector
         }
-        for (int k = 0; k < nsets; ++k)
+        const int nimg = nsets + (kind == ADS_ELASTIC ? 3 : 0);   // per-set images + mixed elastic images
+        for (int k = 0; k < nimg; ++k)
             add(2 * (mp[0] + mp[1]) * W * e + (mp[0] + mp[1]) * e +
                 (ads::line_image_elems(p, (int)S[0]) + ads::line_image_elems(p, (int)S[1])) * e + 64);
     }

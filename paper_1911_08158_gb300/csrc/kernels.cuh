@@ -50,8 +50,9 @@ struct SrcDev {
 };
 
 // Fused RHS + directional sweeps (kernel K1), one z-plane tile per CTA:
-//   out = Ax^{-1} [ F(t) - c2 (Kx.My.Mz + Mx.Ky.Mz + Mx.My.Kz) in ]   (along x)
+//   out = Ax^{-1} [ F(t) - c2 (Kx.My.Mz + Mx.My.Kz + Mx.Ky.Mz) in ]   (along x)
 // and, when the tile spans all of y (ty == my), also Ay^{-1} along y.
+// Direct mode: out = Ax^{-1} [Ay^{-1}] in (the RHS is given).
 // t = (step[0] + toff) * tau.
 template <typename T>
 struct RhsArgs {
@@ -71,6 +72,7 @@ struct RhsArgs {
     double tau;
     int ty;               // rows per tile (y); fused y sweep iff ty == my
     int *err;             // device error word (bounded waits)
+    int direct;           // 1: `in` is the RHS itself (no quadrature): out = Ax^{-1} [Ay^{-1}] in
 };
 
 // Column sweep along y (axis 1) or z (axis 2): 32 x-columns per CTA, one
@@ -146,6 +148,11 @@ cudaError_t launch_rhs_group(int p, const RhsArgs<T> *a, int n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s);
 
+// out = beta*out + alpha*(Ax (x) Ay (x) Az) in in one pass (bands [m_pad][2p+1]
+// of each axis); row padding of out is written as zero
+template <typename T>
+cudaError_t launch_kron3(int p, const T *bx, const T *by, const T *bz, const T *in, T *out, Dims d, T alpha, T beta,
+                         cudaStream_t s);
 // out = band applied along axis (0,1,2) to in; out = beta*out + alpha*(A in)
 template <typename T>
 cudaError_t launch_axis_apply(int p, const T *band, int axis, const T *in, T *out, Dims d, T alpha, T beta,

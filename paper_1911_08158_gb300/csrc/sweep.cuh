@@ -426,8 +426,16 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
     }
     __syncthreads();   // barrier initialised, s_r set
 
-    // ---- phase 1 (overlaps the table copy: its y bands are read from global memory)
-    {
+    if (a.direct) {
+        // ---- phase 1 (direct mode): the RHS is given; stage its rows into S1
+        const T *src0 = a.in + (long long)z * plane + (long long)y0 * sx;
+        for (int l = warp; l < tye; l += nwarps) {
+            const T *src = src0 + (long long)l * sx;
+            T *dst = S1 + (size_t)l * RS;
+            for (int x = lane; x < mx; x += 32) dst[x] = src[x];
+        }
+    } else {
+        // ---- phase 1 (overlaps the table copy: its y bands are read from global memory)
         const T *gMy = a.bandM[1].v, *gKy = a.bandK[1].v;
         T cm[W], ck[W], mym[W], myk[W];
         const int ylo = a.bandM[1].lo, yhi = a.bandM[1].hi;   // K shares M's interior range
@@ -489,7 +497,12 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
         T v[SEG];
 #pragma unroll
         for (int k = 0; k < SEG; ++k) v[k] = T(0);
-        if (on) {
+        if (on && a.direct) {
+            const T *row1 = S1 + (size_t)l * RS;
+#pragma unroll
+            for (int k = 0; k < SEG; ++k) v[k] = (k < n) ? row1[b0 + k] : T(0);
+            seg_pass1<T, P, SEG>(LX.fac + b0 * W, v);
+        } else if (on) {
             const T *row1 = S1 + (size_t)l * RS;
             const T *row2 = S2 + (size_t)l * RS;
             const int y = y0 + l;
@@ -734,13 +747,12 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
     return cudaGetLastError();
 }
 
+// A single simulation is a group of one: one instantiation per (T, P)
+// serves both (its parameters are read with a run-time index, which keeps
+// them out of the register budget of the sweeps).
 template <typename T, int P>
 cudaError_t rhs_group_dispatch(const RhsArgs<T> *a, int n, cudaStream_t s)
 {
-    if (n == 1) {
-        const int o = 0;
-        return rhs_group_p<T, P, 1>(a, &o, 1, s);
-    }
     // heaviest blocks first (rows x columns of a tile) so that the tail of
     // the launch holds the short ones
     std::vector<int> order(n);
@@ -808,10 +820,6 @@ cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *ord
 template <typename T, int P>
 cudaError_t col_group_dispatch(const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s)
 {
-    if (n == 1) {
-        const int o = 0;
-        return col_group_p<T, P, 1>(a, maps, &o, 1, s);
-    }
     auto len = [&](int i) { return a[i].axis == 1 ? a[i].d.my : a[i].d.mz; };
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
