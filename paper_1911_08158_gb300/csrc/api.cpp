@@ -85,7 +85,7 @@ struct ads_sim {
     // scalar-wave state (precision prec): p = u + tau v + eta a, q = tau v + tau^2/2 a
     void *P = nullptr, *Q = nullptr, *A = nullptr, *X = nullptr;
     // elasticity state: U^n, U^{n-1} (3 components, component-major) and work
-    void *U = nullptr, *Up = nullptr, *R = nullptr, *Y = nullptr, *T1 = nullptr, *T2 = nullptr;
+    void *U = nullptr, *Up = nullptr, *R = nullptr, *Y = nullptr;
     void *ebandFP64[3][2] = {};   // bands of M + d K (d = tau^2 c / (4 rho)), FP64, for the invariant
     long long *d_step = nullptr;
     long long h_step = 0;
@@ -699,29 +699,64 @@ int kron3(ads_sim *s, const T *in, T *out, const int *which, T coef, bool accumu
     return ADS_OK;
 }
 
-// out_i = (Ups U)_i, i = 0..2 (component stride cnt)
+// Kronecker term coef * (A0 (x) A1 (x) A2) in; which[a]: 0 = M, 1 = K, 2 = B
 template <typename T>
-int apply_upsilon(ads_sim *s, const T *U, T *out, T *ta, T *tb)
+ads::KronTerm<T> kterm(const ads_sim *s, const int *which, const T *in, T coef)
 {
+    const TableSet &ts = tables_for<T>(s);
+    const void *band[3];
+    for (int a = 0; a < 3; ++a) band[a] = which[a] == 0 ? ts.M[a] : (which[a] == 1 ? ts.K[a] : ts.B[a]);
+    ads::KronTerm<T> t{};
+    t.bx = (const T *)band[0];
+    t.by = (const T *)band[1];
+    t.bz = (const T *)band[2];
+    t.in = in;
+    t.alpha = coef;
+    return t;
+}
+
+template <typename T>
+ads::KronTerm<T> plain_term(const T *in, T coef)
+{
+    ads::KronTerm<T> t{};
+    t.in = in;
+    t.alpha = coef;
+    t.plain = 1;
+    return t;
+}
+
+template <typename T>
+void add_term(ads::KronSum<T> &ks, const ads::KronTerm<T> &t)
+{
+    ks.t[ks.nt++] = t;
+}
+
+// out_i = coef (Ups U)_i, i = 0..2 (component stride cnt), one launch per
+// component:  (Ups U)_i = sum_a c_ia (K on axis a, M elsewhere) U_i
+//                         - (mu + lam) sum_{j != i} (B on axes i, j) U_j,
+// c_ia = mu + (mu + lam) [a == i]
+template <typename T>
+int apply_upsilon(ads_sim *s, const T *U, T *out, T *ta, T *tb, T coef = T(1))
+{
+    (void)ta;
+    (void)tb;
     const long long cnt = s->d.count();
-    const T lm = (T)(s->lam + s->mu);
+    const double lm = s->lam + s->mu;
     for (int i = 0; i < 3; ++i) {
-        T *oi = out + i * cnt;
-        // mu K_lap U_i through K1 with identity factors: K1 returns -c2 K in
-        ads::RhsArgs<T> r = rhs_args<T>(s, U + i * cnt, oi, SET_IDENT, 0, false);
-        r.c2 = (T)(-s->mu);
-        ADS_CK(ads::launch_rhs<T>(s->p, s->seg, r, s->stream));
-        int w[3] = {0, 0, 0};
-        w[i] = 1;
-        int rc = kron3<T>(s, U + i * cnt, oi, w, lm, true, ta, tb);
-        if (rc) return rc;
+        ads::KronSum<T> ks{};
+        for (int a = 0; a < 3; ++a) {
+            int w[3] = {0, 0, 0};
+            w[a] = 1;
+            add_term(ks, kterm<T>(s, w, U + i * cnt, (T)(coef * (s->mu + (a == i ? lm : 0.0)))));
+        }
         for (int j = 0; j < 3; ++j) {
             if (j == i) continue;
             int b[3] = {0, 0, 0};
             b[i] = 2;
             b[j] = 2;
-            if ((rc = kron3<T>(s, U + j * cnt, oi, b, (T)(-lm), true, ta, tb))) return rc;
+            add_term(ks, kterm<T>(s, b, U + j * cnt, (T)(-coef * lm)));
         }
+        ADS_CK(ads::launch_kron_sum<T>(s->p, ks, out + i * cnt, s->d, s->stream));
     }
     return ADS_OK;
 }
@@ -783,48 +818,50 @@ template <typename T>
 int elastic_step(ads_sim *s, KernelTimer *kt = nullptr)
 {
     const long long cnt = s->d.count();
-    T *U = (T *)s->U, *Up = (T *)s->Up, *R = (T *)s->R, *Y = (T *)s->Y, *t1 = (T *)s->T1, *t2 = (T *)s->T2;
+    T *U = (T *)s->U, *Up = (T *)s->Up, *R = (T *)s->R, *Y = (T *)s->Y;
     const T tau2 = (T)(s->tau * s->tau), rho = (T)s->rho;
     const T half = (T)(0.5 * s->tau * s->tau * (s->lam + s->mu) / s->rho);   // (1/2) tau^2 (mu+lam) / rho
     int rc;
+    auto bb = [](int i, int j, int *b) {
+        b[0] = b[1] = b[2] = 0;
+        b[i] = 2;
+        b[j] = 2;
+    };
     if (kt && (rc = kt->mark(s->stream, "elastic_rhs"))) return rc;
-    if ((rc = apply_upsilon<T>(s, U, R, t1, t2))) return rc;
-    ADS_CK(ads::launch_lincomb<T>(R, -tau2, R, T(0), (const T *)nullptr, 3 * cnt, s->stream));
+    // R = tau^2 (f^n - Ups U^n)
+    if ((rc = apply_upsilon<T>(s, U, R, nullptr, nullptr, -tau2))) return rc;
     if ((rc = add_body_force<T>(s, R, s->tau * s->tau, 0))) return rc;
     if (kt && (rc = kt->mark(s->stream, "elastic_lower"))) return rc;
-    // lower: y_i = L~_i^{-1} (r_i - tau^2/2 sum_{j<i} Ups_ij y_j)
+    // lower: y_i = L~_i^{-1} (R_i / rho + (tau^2/2)(mu+lam)/rho sum_{j<i} [B_i B_j M] y_j)
+    //        (-Ups_ij = (mu+lam) [B_i B_j M] with the Dirichlet restriction)
     for (int i = 0; i < 3; ++i) {
-        T *yi = Y + i * cnt;
-        ADS_CK(ads::launch_lincomb<T>(yi, T(1) / rho, R + i * cnt, T(0), (const T *)nullptr, cnt, s->stream));
+        ads::KronSum<T> ks{};
+        add_term(ks, plain_term<T>(R + i * cnt, T(1) / rho));
         for (int j = 0; j < i; ++j) {
-            int b[3] = {0, 0, 0};
-            b[i] = 2;
-            b[j] = 2;
-            if ((rc = kron3<T>(s, Y + j * cnt, yi, b, half, true, t1, t2))) return rc;
+            int b[3];
+            bb(i, j, b);
+            add_term(ks, kterm<T>(s, b, Y + j * cnt, half));
         }
-        if ((rc = elastic_diag_solve<T>(s, i, yi))) return rc;
-    }
-    if (kt && (rc = kt->mark(s->stream, "elastic_mass"))) return rc;
-    // s = rho M y  (into R)
-    for (int i = 0; i < 3; ++i) {
-        const int m3[3] = {0, 0, 0};
-        if ((rc = kron3<T>(s, Y + i * cnt, R + i * cnt, m3, rho, false, t1, t2))) return rc;
+        ADS_CK(ads::launch_kron_sum<T>(s->p, ks, Y + i * cnt, s->d, s->stream));
+        if ((rc = elastic_diag_solve<T>(s, i, Y + i * cnt))) return rc;
     }
     if (kt && (rc = kt->mark(s->stream, "elastic_upper"))) return rc;
-    // upper: delta_i = L~_i^{-1} (s_i - tau^2/2 sum_{j>i} Ups_ij delta_j), delta stored in Y
+    // rho M y, then upper: delta_i = L~_i^{-1} (M y_i + half sum_{j>i} [B_i B_j M] delta_j),
+    // delta stored in R
     for (int i = 2; i >= 0; --i) {
-        T *yi = Y + i * cnt;
-        ADS_CK(ads::launch_lincomb<T>(yi, T(1) / rho, R + i * cnt, T(0), (const T *)nullptr, cnt, s->stream));
+        ads::KronSum<T> ks{};
+        const int m3[3] = {0, 0, 0};
+        add_term(ks, kterm<T>(s, m3, Y + i * cnt, T(1)));
         for (int j = i + 1; j < 3; ++j) {
-            int b[3] = {0, 0, 0};
-            b[i] = 2;
-            b[j] = 2;
-            if ((rc = kron3<T>(s, Y + j * cnt, yi, b, half, true, t1, t2))) return rc;
+            int b[3];
+            bb(i, j, b);
+            add_term(ks, kterm<T>(s, b, R + j * cnt, half));
         }
-        if ((rc = elastic_diag_solve<T>(s, i, yi))) return rc;
+        ADS_CK(ads::launch_kron_sum<T>(s->p, ks, R + i * cnt, s->d, s->stream));
+        if ((rc = elastic_diag_solve<T>(s, i, R + i * cnt))) return rc;
     }
     if (kt && (rc = kt->mark(s->stream, "elastic_update"))) return rc;
-    ADS_CK(ads::launch_atm_update<T>(U, Up, Y, 3 * cnt, s->d_step, s->stream));
+    ADS_CK(ads::launch_atm_update<T>(U, Up, R, 3 * cnt, s->d_step, s->stream));
     if (kt && (rc = kt->mark(s->stream, ""))) return rc;
     return ADS_OK;
 }
@@ -1364,9 +1401,7 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
         s->Up = dalloc(s, 3 * n);
         s->R = dalloc(s, 3 * n);
         s->Y = dalloc(s, 3 * n);
-        s->T1 = dalloc(s, n);
-        s->T2 = dalloc(s, n);
-        ok = ok && s->U && s->Up && s->R && s->Y && s->T1 && s->T2;
+        ok = ok && s->U && s->Up && s->R && s->Y;
         // bands of M + d K for the discrete invariant (FP64)
         for (int a = 0; a < 3 && ok; ++a)
             for (int k = 0; k < 2 && ok; ++k) {
@@ -1385,8 +1420,6 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     }
     for (void *q : {s->P, s->Q, s->A, s->X, s->U, s->Up, s->R, s->Y})
         if (q) cudaMemsetAsync(q, 0, q == s->U || q == s->Up || q == s->R || q == s->Y ? 3 * n : n, s->stream);
-    for (void *q : {s->T1, s->T2})
-        if (q) cudaMemsetAsync(q, 0, n, s->stream);
     cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->stream);
     cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
     static unsigned long long next_uid = 0;
@@ -1821,8 +1854,6 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
         for (int i = 0; i < 4; ++i) add(cnt * el);
     } else {
         for (int i = 0; i < 4; ++i) add(3 * cnt * el);
-        add(cnt * el);
-        add(cnt * el);
         for (int a = 0; a < 3; ++a) add(2 * mp[a] * W * 8);
     }
     const int nsets = kind == ADS_SCALAR_WAVE ? 3 : 4;

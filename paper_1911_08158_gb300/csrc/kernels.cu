@@ -121,6 +121,88 @@ __global__ void __launch_bounds__(256) k_kron3(const T *__restrict__ bx, const T
     }
 }
 
+// Sum of Kronecker products, one CTA per (z-plane, tile of ty rows): the
+// terms are applied one after another through two staging buffers
+// (z-contraction, y-contraction) and accumulated into a third, which is
+// stored once.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_kron_sum(const __grid_constant__ KronSum<T> ks, T *out, Dims d, int ty)
+{
+    constexpr int W = 2 * P + 1;
+    extern __shared__ __align__(16) unsigned char ksum_smem[];
+    const int sx = d.sx, mx = d.mx, my = d.my, mz = d.mz;
+    T *Tz = reinterpret_cast<T *>(ksum_smem);   // [(ty + 2P)][sx]
+    T *Uy = Tz + (size_t)(ty + 2 * P) * sx;     // [ty][sx]
+    T *O = Uy + (size_t)ty * sx;                // [ty][sx] accumulator
+    const int z = blockIdx.y, y0 = blockIdx.x * ty;
+    const int tye = min(ty, my - y0);
+    const long long plane = d.plane();
+    const long long base = (long long)z * plane + (long long)y0 * sx;
+    for (int idx = threadIdx.x; idx < tye * mx; idx += blockDim.x) {
+        const int l = idx / mx, x = idx - l * mx;
+        O[(size_t)l * sx + x] = ks.beta == T(0) ? T(0) : ks.beta * out[base + (long long)l * sx + x];
+    }
+    for (int t = 0; t < ks.nt; ++t) {
+        const KronTerm<T> &tm = ks.t[t];
+        if (tm.plain) {
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < tye * mx; idx += blockDim.x) {
+                const int l = idx / mx, x = idx - l * mx;
+                O[(size_t)l * sx + x] += tm.alpha * tm.in[base + (long long)l * sx + x];
+            }
+            continue;
+        }
+        T cz[W];
+        bool zok[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            cz[k] = tm.bz[z * W + k];
+            zok[k] = z + k - P >= 0 && z + k - P < mz;
+        }
+        __syncthreads();   // previous term's reads of Tz / Uy are done
+        const int nr = tye + 2 * P;
+        for (int idx = threadIdx.x; idx < nr * mx; idx += blockDim.x) {
+            const int r = idx / mx, x = idx - r * mx;
+            const int y = y0 - P + r;
+            T acc = T(0);
+            if (y >= 0 && y < my) {
+                const T *src = tm.in + (long long)(z - P) * plane + (long long)y * sx + x;
+#pragma unroll
+                for (int k = 0; k < W; ++k)
+                    if (zok[k]) acc += cz[k] * src[(long long)k * plane];
+            }
+            Tz[(size_t)r * sx + x] = acc;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < tye * mx; idx += blockDim.x) {
+            const int l = idx / mx, x = idx - l * mx;
+            const T *row = tm.by + (size_t)(y0 + l) * W;
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < W; ++q) acc += row[q] * Tz[(size_t)(l + q) * sx + x];
+            Uy[(size_t)l * sx + x] = acc;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < tye * mx; idx += blockDim.x) {
+            const int l = idx / mx, x = idx - l * mx;
+            const T *row = tm.bx + (size_t)x * W;
+            const T *u = Uy + (size_t)l * sx;
+            T acc = T(0);
+#pragma unroll
+            for (int r = 0; r < W; ++r) {
+                const int xx = x + r - P;
+                if (xx >= 0 && xx < mx) acc += row[r] * u[xx];
+            }
+            O[(size_t)l * sx + x] += tm.alpha * acc;
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < tye * sx; idx += blockDim.x) {
+        const int l = idx / sx, x = idx - l * sx;
+        out[base + (long long)l * sx + x] = x < mx ? O[(size_t)l * sx + x] : T(0);
+    }
+}
+
 template <typename T, int P>
 __global__ void k_solve_x(const T *__restrict__ F, T *data, Dims d)
 {
@@ -504,6 +586,38 @@ cudaError_t launch_axis_apply(int p, const T *band, int axis, const T *in, T *ou
 }
 
 template <typename T, int P>
+cudaError_t kron_sum_impl(dim3 grid, size_t smem, cudaStream_t s, const KronSum<T> &ks, T *out, Dims d, int ty)
+{
+    static size_t smem_set = 48 * 1024;   // per instantiation: opt-in dynamic shared memory (set outside capture)
+    if (smem > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_kron_sum<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    k_kron_sum<T, P><<<grid, 256, smem, s>>>(ks, out, d, ty);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_kron_sum(int p, const KronSum<T> &ks, T *out, Dims d, cudaStream_t s)
+{
+    if (ks.nt < 0 || ks.nt > kMaxKronTerms) return cudaErrorInvalidValue;
+    // rows per tile: three buffers within 120 KB of shared memory
+    const size_t row = (size_t)d.sx * sizeof(T);
+    int ty = (int)((120 * 1024 / row - 2 * p) / 3);
+    if (ty > 16) ty = 16;
+    if (ty < 1) ty = 1;
+    if (ty > d.my) ty = d.my;
+    const size_t smem = (size_t)(3 * ty + 2 * p) * row;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    dim3 grid((d.my + ty - 1) / ty, d.mz);
+    ++g_launches;
+#define C(P) kron_sum_impl<T, P>(grid, smem, s, ks, out, d, ty)
+    ADS_DISPATCH_P(p, C)
+#undef C
+}
+
+template <typename T, int P>
 cudaError_t kron3_impl(dim3 grid, size_t smem, cudaStream_t s, const T *bx, const T *by, const T *bz, const T *in,
                        T *out, Dims d, T alpha, T beta, int ty)
 {
@@ -690,6 +804,7 @@ cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long 
     template cudaError_t launch_axis_apply<T>(int, const T *, int, const T *, T *, Dims, T, T, int, cudaStream_t); \
     template cudaError_t launch_solve_x<T>(int, const T *, T *, Dims, cudaStream_t);                               \
     template cudaError_t launch_kron3<T>(int, const T *, const T *, const T *, const T *, T *, Dims, T, T, cudaStream_t); \
+    template cudaError_t launch_kron_sum<T>(int, const KronSum<T> &, T *, Dims, cudaStream_t);                     \
     template cudaError_t launch_pack<T>(const double *, T *, Dims, double, cudaStream_t);                          \
     template cudaError_t launch_unpack<T>(const T *, double *, Dims, cudaStream_t);                                \
     template cudaError_t launch_uva_to_pq<T>(const double *, const double *, const double *, T *, T *, T *, Dims,  \

@@ -148,6 +148,25 @@ cudaError_t launch_rhs_group(int p, const RhsArgs<T> *a, int n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s);
 
+// Sum of Kronecker products in one pass:
+//   out = beta*out + sum_t alpha_t (Ax_t (x) Ay_t (x) Az_t) in_t
+// (plain terms: alpha_t in_t, no contraction); row padding written as zero.
+constexpr int kMaxKronTerms = 6;
+template <typename T>
+struct KronTerm {
+    const T *bx, *by, *bz;   // bands [m_pad][2p+1] per axis
+    const T *in;
+    T alpha;
+    int plain;
+};
+template <typename T>
+struct KronSum {
+    KronTerm<T> t[kMaxKronTerms];
+    int nt;
+    T beta;
+};
+template <typename T>
+cudaError_t launch_kron_sum(int p, const KronSum<T> &ks, T *out, Dims d, cudaStream_t s);
 // out = beta*out + alpha*(Ax (x) Ay (x) Az) in in one pass (bands [m_pad][2p+1]
 // of each axis); row padding of out is written as zero
 template <typename T>
