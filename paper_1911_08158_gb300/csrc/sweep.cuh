@@ -220,6 +220,13 @@ struct Vec2<float> { using type = float2; };
 template <>
 struct Vec2<double> { using type = double2; };
 
+// c + a * b on a pair of columns: one packed FP32 FMA (FFMA2) for float
+__device__ __forceinline__ float2 fma2(float a, float2 b, float2 c) { return __ffma2_rn(make_float2(a, a), b, c); }
+__device__ __forceinline__ double2 fma2(double a, double2 b, double2 c)
+{
+    return make_double2(fma(a, b.x, c.x), fma(a, b.y, c.y));
+}
+
 template <typename T, int P, bool GUARD, bool INTERIOR>
 __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int sx, int my, const bool (&zok)[2 * P + 1],
                                              const T (&cm)[2 * P + 1], const T (&ck)[2 * P + 1],
@@ -228,9 +235,9 @@ __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int
 {
     constexpr int W = 2 * P + 1;
     using V2 = typename Vec2<T>::type;
-    T r1[W][2], r2[W][2];
+    V2 r1[W], r2[W];   // ring of z-contracted rows (t1 = Mz p, t2 = Kz p) for the column pair
 #pragma unroll
-    for (int k = 0; k < W; ++k) r1[k][0] = r1[k][1] = r2[k][0] = r2[k][1] = T(0);
+    for (int k = 0; k < W; ++k) r1[k] = r2[k] = V2{T(0), T(0)};
     const int n = ye - yb + 2 * P;
     const T *rowp = col0 + (long long)(yb - P) * sx;
     for (int r0 = 0; r0 < n; r0 += W) {
@@ -246,16 +253,14 @@ __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int
                 const bool okk = GUARD ? (ok && zok[k]) : ok;
                 v[k] = okk ? *reinterpret_cast<const V2 *>(c + (long long)k * plane) : V2{T(0), T(0)};
             }
-            T t10 = T(0), t11 = T(0), t20 = T(0), t21 = T(0);
+            V2 t1 = V2{T(0), T(0)}, t2 = V2{T(0), T(0)};
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                t10 += cm[k] * v[k].x;
-                t11 += cm[k] * v[k].y;
-                t20 += ck[k] * v[k].x;
-                t21 += ck[k] * v[k].y;
+                t1 = fma2(cm[k], v[k], t1);
+                t2 = fma2(ck[k], v[k], t2);
             }
-            r1[j][0] = t10; r1[j][1] = t11;
-            r2[j][0] = t20; r2[j][1] = t21;
+            r1[j] = t1;
+            r2[j] = t2;
             if (r >= 2 * P && r < n) {
                 const int y = yb + r - 2 * P;
                 T bm[W], bk[W];
@@ -266,20 +271,19 @@ __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int
                     band_row<T, W>(bMy, ylo, yhi, mym, y, bm);
                     band_row<T, W>(bKy, ylo, yhi, myk, y, bk);
                 }
-                T a0 = T(0), a1 = T(0), c0 = T(0), c1 = T(0);
+                V2 a = V2{T(0), T(0)}, c = V2{T(0), T(0)};
 #pragma unroll
                 for (int q = 0; q < W; ++q) {
                     // window row y-P+q = stream index r-2P+q  ->  ring slot (j-2P+q) mod W
                     const int sl = (j - 2 * P + q + 2 * W) % W;
-                    a0 += bm[q] * r1[sl][0];
-                    a1 += bm[q] * r1[sl][1];
-                    c0 += bk[q] * r1[sl][0] + bm[q] * r2[sl][0];
-                    c1 += bk[q] * r1[sl][1] + bm[q] * r2[sl][1];
+                    a = fma2(bm[q], r1[sl], a);
+                    c = fma2(bk[q], r1[sl], c);
+                    c = fma2(bm[q], r2[sl], c);
                 }
-                s1col[(size_t)y * RS] = a0;
-                s1col[(size_t)y * RS + 1] = a1;
-                s2col[(size_t)y * RS] = c0;
-                s2col[(size_t)y * RS + 1] = c1;
+                s1col[(size_t)y * RS] = a.x;
+                s1col[(size_t)y * RS + 1] = a.y;
+                s2col[(size_t)y * RS] = c.x;
+                s2col[(size_t)y * RS + 1] = c.y;
             }
         }
     }
