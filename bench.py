@@ -221,7 +221,8 @@ def run_ours(args):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",
                 "kernel_share": {k: round(v / sum(tot.values()), 4) for k, v in tot.items()},
-                "kernel_ms": {k: round(v, 5) for k, v in tot.items()}}
+                "kernel_ms": {k: round(v, 5) for k, v in tot.items()},
+                "kernel_ms_by_p": {"%s_p%d" % (n, pp): round(float(np.mean(v)), 5) for (n, pp), v in kt.items()}}
     # the whole step: K1 reads p and writes x (8 B), K3 reads x, p, q and
     # writes p, q (20 B) per interior DOF; a is stored once per 16 steps
     interior = sum((s.n[0] - 2) * (s.n[1] - 2) * (s.n[2] - 2) for s in sims)

@@ -47,6 +47,7 @@ struct LineTables {
     void *base = nullptr;
     int S = 0;
     int bytes = 0;
+    int seg = 32;
 };
 
 enum { SET_SPLIT = 0, SET_MASS = 1, SET_IDENT = 2, SET_ELAS0 = 3, SET_ELAS1 = 4, NSETS = 5 };
@@ -271,6 +272,7 @@ int upload_line(ads_sim *s, int set, int axis, LineTables *lt)
 {
     int rc = upload_padded<T>(s, s->hline[set][axis], &lt->base, &lt->bytes);
     lt->S = s->lineS[axis];
+    lt->seg = s->seg;
     return rc;
 }
 
@@ -328,6 +330,7 @@ ads::LineDev<T> line_dev(const LineTables &lt)
     l.base = (const T *)lt.base;
     l.S = lt.S;
     l.bytes = lt.bytes;
+    l.seg = lt.seg;
     return l;
 }
 
@@ -342,7 +345,7 @@ void choose_tiles(ads_sim *s)
         const size_t budget_fused = 220 * 1024, budget = 110 * 1024;
         const char *env = std::getenv("ADS_RHS_TILE");   // rows per tile, for experiments
         int ty = 0;
-        auto fits = [&](int t, size_t b) { return ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy) <= b; };
+        auto fits = [&](int t, size_t b) { return ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy, s->seg) <= b; };
         if (env && std::sscanf(env, "%d", &ty) == 1 && ty > 0) {
             ty = std::min(ty, my);
             if (!fits(ty, budget_fused)) ty = 0;
@@ -1120,9 +1123,9 @@ std::vector<int> tile_candidates(const ads_sim *s)
     const int el = (int)elem(s);
     const int Sx = segs(s, s->d.mx), Sy = segs(s, s->d.my), my = s->d.my;
     std::vector<int> c;
-    if (ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy) <= 220 * 1024) c.push_back(my);
+    if (ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg) <= 220 * 1024) c.push_back(my);
     for (int t : {8, 16, 32, 64})
-        if (t < my && ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy) <= 220 * 1024) c.push_back(t);
+        if (t < my && ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy, s->seg) <= 220 * 1024) c.push_back(t);
     return c;
 }
 
@@ -1363,7 +1366,10 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     s->d.my = s->ax[1].m;
     s->d.mz = s->ax[2].m;
     s->d.sx = (s->d.mx + 7) / 8 * 8;
-    s->seg = 32;
+    {
+        const int m3[3] = {s->d.mx, s->d.my, s->d.mz};
+        s->seg = ads::choose_seg(m3);   // 33-row segments when they save segments (m = 32 s + 1)
+    }
     choose_tiles(s);
     if (o.tile_lines > 0) {
         // user override of the tile height (rows of one z-plane per CTA)
@@ -1836,12 +1842,17 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
         (precision != ADS_FP64 && precision != ADS_FP32))
         return 0;
     size_t m[3], mp[3], S[3];
+    int mi[3];
     for (int a = 0; a < 3; ++a) {
         const long long me = (long long)grid->n_elem[a] + p - 2;
-        if (grid->n_elem[a] < 1 || me < 1) return 0;
+        if (grid->n_elem[a] < 1 || me < 1 || me > (1 << 20)) return 0;
         m[a] = (size_t)me;
-        S[a] = (m[a] + ads::kSeg - 1) / ads::kSeg;
-        mp[a] = S[a] * ads::kSeg;
+        mi[a] = (int)me;
+    }
+    const int seg = ads::choose_seg(mi);
+    for (int a = 0; a < 3; ++a) {
+        S[a] = (m[a] + seg - 1) / seg;
+        mp[a] = S[a] * seg;
     }
     const size_t W = 2 * (size_t)p + 1, el = precision == ADS_FP64 ? 8 : 4;
     const size_t cnt = (m[0] + 7) / 8 * 8 * m[1] * m[2];
@@ -1861,14 +1872,14 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
         const size_t e = t == 0 ? 8 : 4;
         for (int a = 0; a < 3; ++a) {
             add(3 * mp[a] * W * e + 64);                                    // M, K, B
-            for (int k = 0; k < nsets; ++k) add(ads::line_image_elems(p, (int)S[a]) * e + 64);
+            for (int k = 0; k < nsets; ++k) add(ads::line_image_elems(p, (int)S[a], seg) * e + 64);
             add(mp[a] * W * e);                                             // bands of M + eta K
             add(mp[a] * e);                                                 // source load vector
         }
         const int nimg = nsets + (kind == ADS_ELASTIC ? 3 : 0);   // per-set images + mixed elastic images
         for (int k = 0; k < nimg; ++k)
             add(2 * (mp[0] + mp[1]) * W * e + (mp[0] + mp[1]) * e +
-                (ads::line_image_elems(p, (int)S[0]) + ads::line_image_elems(p, (int)S[1])) * e + 64);
+                (ads::line_image_elems(p, (int)S[0], seg) + ads::line_image_elems(p, (int)S[1], seg)) * e + 64);
     }
     return b;
 }

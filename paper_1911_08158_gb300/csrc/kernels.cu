@@ -521,16 +521,17 @@ bool make_update_maps(ColMaps *m, const void *P, const void *Q, int elem, const 
 namespace {
 }  // namespace
 
-size_t line_image_elems(int p, int S) { return (size_t)line_image_elems_dev(p, S * kSeg, S); }
+size_t line_image_elems(int p, int S, int seg) { return (size_t)line_image_elems_dev(p, S * seg, S); }
 
-size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy)
+size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy, int seg)
 {
-    const int W = 2 * p + 1, mxp = Sx * kSeg, myp = Sy * kSeg;
+    const int W = 2 * p + 1, mxp = Sx * seg, myp = Sy * seg;
     (void)d;
-    return 2 * (size_t)mxp * W + 2 * (size_t)myp * W + mxp + myp + line_image_elems(p, Sx) + line_image_elems(p, Sy);
+    return 2 * (size_t)mxp * W + 2 * (size_t)myp * W + mxp + myp + line_image_elems(p, Sx, seg) +
+           line_image_elems(p, Sy, seg);
 }
 
-size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy)
+size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg)
 {
     const int RS = ((d.mx + 1) & ~1) | 1;
     const int rows_pad = (ty + 31) & ~31, cols_pad = (d.mx + 31) & ~31;
@@ -538,16 +539,26 @@ size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy)
     const int cld = (fuse && cols_pad > rows_pad) ? cols_pad : rows_pad;
     const int Smax = (fuse && Sy > Sx) ? Sy : Sx;
     size_t n = 2 * (size_t)ty * RS + 2 * (size_t)Smax * p * cld;
-    return n * elem + 16 + ((rhs_image_elems(p, d, Sx, Sy) * elem + 15) & ~(size_t)15);
+    return n * elem + 16 + ((rhs_image_elems(p, d, Sx, Sy, seg) * elem + 15) & ~(size_t)15);
+}
+
+int choose_seg(const int *m)
+{
+    int n32 = 0, n33 = 0;
+    for (int a = 0; a < 3; ++a) {
+        n32 += (m[a] + kSeg - 1) / kSeg;
+        n33 += (m[a] + kSegAlt - 1) / kSegAlt;
+    }
+    return n33 < n32 ? kSegAlt : kSeg;
 }
 
 int rhs_threads(int elem) { return elem == 8 ? 256 : 512; }
 
-size_t col_smem_bytes(int p, int elem, int len, int S)
+size_t col_smem_bytes(int p, int elem, int len, int S, int seg)
 {
     (void)len;
     size_t n = 2 * (size_t)S * p * 32;
-    return n * elem + 16 + ((line_image_elems(p, S) * elem + 15) & ~(size_t)15);
+    return n * elem + 16 + ((line_image_elems(p, S, seg) * elem + 15) & ~(size_t)15);
 }
 
 #define ADS_DISPATCH_P(p, CALL)                      \
@@ -562,14 +573,14 @@ size_t col_smem_bytes(int p, int elem, int len, int S)
 template <typename T>
 cudaError_t launch_rhs(int p, int seg, const RhsArgs<T> &a, cudaStream_t s)
 {
-    if (seg != kSeg) return cudaErrorInvalidValue;
+    if (seg != kSeg && seg != kSegAlt) return cudaErrorInvalidValue;
     return launch_rhs_group<T>(p, &a, 1, s);
 }
 
 template <typename T>
 cudaError_t launch_col(int p, int seg, const ColArgs<T> &a, cudaStream_t s)
 {
-    if (seg != kSeg) return cudaErrorInvalidValue;
+    if (seg != kSeg && seg != kSegAlt) return cudaErrorInvalidValue;
     return launch_col_group<T>(p, &a, nullptr, 1, s);
 }
 

@@ -9,7 +9,8 @@ namespace ads {
 // device error codes written to a simulation's error word by bounded waits
 enum { kDevErrTimeout = 1, kDevErrAlign = 2 };
 
-constexpr int kSeg = 32;     // rows per register segment of the line solves
+constexpr int kSeg = 32;     // rows per register segment of the line solves ...
+constexpr int kSegAlt = 33;  // ... or 33, when that saves segments (m = 32 s + 1 -> s segments)
 constexpr int kBatch = 32;   // simulations per grouped launch
 
 // Interior field layout on the device: [z][y][x], x fastest, row pitch sx
@@ -25,13 +26,14 @@ struct Dims {
 // solutions [m][p], transfer matrices [S][p][p], segment bounds [S+1].
 // One contiguous buffer, in this order (T elements, no gaps):
 //   fac [m_pad][2p+1] | phi [m_pad][p] | psi [m_pad][p] | Phi [S][p][p] | Psi [S][p][p]
-// with m_pad = S * SEG; segment s = rows [s*SEG, (s+1)*SEG).  It is copied
+// with m_pad = S * seg; segment s = rows [s*seg, (s+1)*seg).  It is copied
 // to shared memory verbatim (one bulk copy) by the sweep kernels.
 template <typename T>
 struct LineDev {
     const T *base;
     int S;
     int bytes;            // padded to 16
+    int seg;              // rows per segment (kSeg or kSegAlt)
 };
 
 // Operator band of one axis with its Toeplitz interior rows [lo, hi).
@@ -129,12 +131,15 @@ struct ColGroup {
 };
 
 // seg: register segment width of the partitioned solves (32)
-size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy);
+size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg);
 int rhs_threads(int elem);
 // element offsets of the K1 table image: returns total elements
-size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy);
-size_t line_image_elems(int p, int S);
-size_t col_smem_bytes(int p, int elem, int len, int S);
+size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy, int seg);
+size_t line_image_elems(int p, int S, int seg);
+size_t col_smem_bytes(int p, int elem, int len, int S, int seg);
+// segment length for a space with interior sizes m[3]: kSegAlt when it
+// needs fewer segments in all than kSeg
+int choose_seg(const int *m);
 
 template <typename T>
 cudaError_t launch_rhs(int p, int seg, const RhsArgs<T> &a, cudaStream_t s);

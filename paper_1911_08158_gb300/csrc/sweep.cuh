@@ -84,6 +84,9 @@ __device__ __forceinline__ LineSm<T> line_carve(T *base, int m, int S)
 // The 1D tables are padded to whole segments (identity factor rows, zero
 // fundamental solutions beyond the line end), so every segment is full and
 // the passes need no predicates.  fb/pb: the segment's rows of fac/phi.
+// The recurrences below subtract the oldest neighbour first and the newest
+// (v[k-1], resp. v[k+1]) last, so only one FMA per row sits on the chain
+// that runs through the segment; everything else overlaps it.
 template <typename T, int P, int SEG>
 __device__ __forceinline__ void seg_pass1(const T *fb, T (&v)[SEG])
 {
@@ -92,7 +95,7 @@ __device__ __forceinline__ void seg_pass1(const T *fb, T (&v)[SEG])
     for (int k = 0; k < SEG; ++k) {
         T w = v[k];
 #pragma unroll
-        for (int q = 1; q <= P; ++q)
+        for (int q = P; q >= 1; --q)
             if (k - q >= 0) w -= fb[k * W + P - q] * v[k - q];
         v[k] = w;
     }
@@ -102,13 +105,19 @@ template <typename T, int P, int SEG>
 __device__ __forceinline__ void seg_pass2(const T *fb, const T *pb, const T (&c)[P], T (&v)[SEG])
 {
     constexpr int W = 2 * P + 1;
+    // forward correction first: independent per row, off the chain
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) {
+        T w = v[k];
+#pragma unroll
+        for (int q = 0; q < P; ++q) w += c[q] * pb[k * P + q];
+        v[k] = w;
+    }
 #pragma unroll
     for (int k = SEG - 1; k >= 0; --k) {
         T w = v[k];
 #pragma unroll
-        for (int q = 0; q < P; ++q) w += c[q] * pb[k * P + q];
-#pragma unroll
-        for (int q = 1; q <= P; ++q)
+        for (int q = P; q >= 1; --q)
             if (k + q < SEG) w -= fb[k * W + P + q] * v[k + q];
         v[k] = w * fb[k * W + P];
     }
@@ -332,15 +341,15 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
 #pragma unroll
             for (int q = 0; q < W; ++q) { bm[q] = mxm[q]; bk[q] = mxk[q]; }
         }
-        T acc = T(0);
+        T acc1 = T(0), acc2 = T(0);   // two independent chains
 #pragma unroll
-        for (int q = 0; q < W; ++q) acc += bk[q] * a1[k + q] + bm[q] * a2[k + q];
-        T w = (fxb ? rowF * fxb[k] : T(0)) - c2 * acc;
-#pragma unroll
-        for (int q = 1; q <= P; ++q)
-            if (k - q >= 0) w -= fb[k * W + P - q] * v[k - q];
-        v[k] = w;
+        for (int q = 0; q < W; ++q) {
+            acc1 += bk[q] * a1[k + q];
+            acc2 += bm[q] * a2[k + q];
+        }
+        v[k] = (fxb ? rowF * fxb[k] : T(0)) - c2 * (acc1 + acc2);
     }
+    seg_pass1<T, P, SEG>(fb, v);   // rows are independent above; the chain is here
 }
 
 // ---------------------------------------------------------------- K1
@@ -374,14 +383,13 @@ __device__ __forceinline__ int group_find(const int *off, int n, int b)
     return lo;
 }
 
-template <typename T, int P, int NB>
+template <typename T, int P, int NB, int SEG>
 __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_constant__ RhsGroup<T, NB> g)
 {
     const int gs = NB > 1 ? group_find(g.off, g.n, blockIdx.x) : 0;
     const RhsArgs<T> &a = g.a[gs];
     const int lb = blockIdx.x - g.off[gs];   // block within this simulation
     constexpr int W = 2 * P + 1;
-    constexpr int SEG = kSeg;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T s_r;
     const int mx = a.d.mx, my = a.d.my, mz = a.d.mz, sx = a.d.sx;
@@ -591,7 +599,7 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
 // update of the (p, q) state, whose p and q tiles [len][32] are fetched by
 // TMA at kernel start (overlapping the solve), updated in shared memory and
 // written back by TMA stores.
-template <typename T, int P, int NB>
+template <typename T, int P, int NB, int SEG>
 __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T, NB> g)
 {
     const int gs = NB > 1 ? group_find(g.off, g.n, blockIdx.x) : 0;
@@ -599,7 +607,6 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
     const ColMaps &maps = g.maps[gs];
     const int box = g.box[gs];
     const int blk = blockIdx.x - g.off[gs];   // block within this simulation
-    constexpr int SEG = kSeg;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     const Dims d = a.d;
@@ -708,11 +715,11 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
 // ---------------------------------------------------------------- launchers
 
 template <typename T>
-bool rhs_entry_ok(const RhsArgs<T> &a)
+bool rhs_entry_ok(const RhsArgs<T> &a, int seg)
 {
     return a.d.mx > 0 && a.d.my > 0 && a.d.mz > 0 && a.ty > 0 && a.ty <= a.d.my && a.lx.S <= 16 &&
-           a.ly.S <= 16 && a.lx.S * kSeg >= a.d.mx && a.ly.S * kSeg >= a.d.my && a.img && !(a.img_bytes & 15) &&
-           !((uintptr_t)a.img & 15);
+           a.ly.S <= 16 && a.lx.seg == seg && a.ly.seg == seg && a.lx.S * seg >= a.d.mx &&
+           a.ly.S * seg >= a.d.my && a.img && !(a.img_bytes & 15) && !((uintptr_t)a.img & 15);
 }
 
 template <typename T>
@@ -722,7 +729,7 @@ int rhs_blocks(const RhsArgs<T> &a)
 }
 
 // one launch of up to NB simulations, entries a[order[0..n)]
-template <typename T, int P, int NB>
+template <typename T, int P, int NB, int SEG>
 cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream_t s)
 {
     RhsGroup<T, NB> g;
@@ -731,22 +738,22 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
     long long blocks = 0;
     for (int k = 0; k < n; ++k) {
         const RhsArgs<T> &e = a[order[k]];
-        if (!rhs_entry_ok(e)) return cudaErrorInvalidValue;
+        if (!rhs_entry_ok(e, SEG)) return cudaErrorInvalidValue;
         g.a[k] = e;
         g.off[k] = (int)blocks;
         blocks += rhs_blocks(e);
-        smem = std::max(smem, rhs_smem_bytes(P, sizeof(T), e.d, e.ty, e.lx.S, e.ly.S));
+        smem = std::max(smem, rhs_smem_bytes(P, sizeof(T), e.d, e.ty, e.lx.S, e.ly.S, SEG));
     }
     if (blocks <= 0 || blocks > (1ll << 30)) return cudaErrorInvalidValue;
     g.off[n] = (int)blocks;
     g.n = n;
     static size_t smem_set = 48 * 1024;   // per instantiation: opt-in dynamic shared memory
     if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rhs<T, P, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_rhs<T, P, NB, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    k_rhs<T, P, NB><<<(unsigned)blocks, RhsThreads<T>::value, smem, s>>>(g);
+    k_rhs<T, P, NB, SEG><<<(unsigned)blocks, RhsThreads<T>::value, smem, s>>>(g);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -759,27 +766,36 @@ cudaError_t rhs_group_dispatch(const RhsArgs<T> *a, int n, cudaStream_t s)
 {
     // heaviest blocks first (rows x columns of a tile) so that the tail of
     // the launch holds the short ones
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
-        return (long long)a[i].ty * a[i].d.mx > (long long)a[j].ty * a[j].d.mx;
-    });
-    for (int k0 = 0; k0 < n; k0 += kBatch) {
-        cudaError_t e = rhs_group_p<T, P, kBatch>(a, order.data() + k0, std::min(kBatch, n - k0), s);
-        if (e != cudaSuccess) return e;
+    for (int i = 0; i < n; ++i)
+        if (a[i].lx.seg != kSeg && a[i].lx.seg != kSegAlt) return cudaErrorInvalidValue;
+    for (int seg : {kSeg, kSegAlt}) {
+        std::vector<int> order;
+        for (int i = 0; i < n; ++i)
+            if (a[i].lx.seg == seg) order.push_back(i);
+        std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
+            return (long long)a[i].ty * a[i].d.mx > (long long)a[j].ty * a[j].d.mx;
+        });
+        const int m = (int)order.size();
+        for (int k0 = 0; k0 < m; k0 += kBatch) {
+            cudaError_t e = seg == kSeg ? rhs_group_p<T, P, kBatch, kSeg>(a, order.data() + k0, std::min(kBatch, m - k0), s)
+                                        : rhs_group_p<T, P, kBatch, kSegAlt>(a, order.data() + k0,
+                                                                             std::min(kBatch, m - k0), s);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
 
 template <typename T>
-bool col_entry_ok(const ColArgs<T> &a)
+bool col_entry_ok(const ColArgs<T> &a, int seg)
 {
     const int len = a.axis == 1 ? a.d.my : a.d.mz;
-    return (a.axis == 1 || a.axis == 2) && a.d.mx > 0 && len > 0 && a.ln.S * kSeg >= len && a.ln.S <= 16 &&
+    return (a.axis == 1 || a.axis == 2) && a.d.mx > 0 && len > 0 && a.ln.seg == seg && a.ln.S * seg >= len &&
+           a.ln.S <= 16 &&
            a.ln.base && !(a.ln.bytes & 15) && !((uintptr_t)a.ln.base & 15) && (a.mode == 0 || a.mode == 1);
 }
 
-template <typename T, int P, int NB>
+template <typename T, int P, int NB, int SEG>
 cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *order, int n, cudaStream_t s)
 {
     ColGroup<T, NB> g;
@@ -790,7 +806,7 @@ cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *ord
     for (int k = 0; k < n; ++k) {
         const int i = order[k];
         const ColArgs<T> &e = a[i];
-        if (!col_entry_ok(e)) return cudaErrorInvalidValue;
+        if (!col_entry_ok(e, SEG)) return cudaErrorInvalidValue;
         const int len = e.axis == 1 ? e.d.my : e.d.mz;
         const int outer = e.axis == 1 ? e.d.mz : e.d.my;
         const int box = col_box(len);
@@ -804,7 +820,7 @@ cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *ord
         g.box[k] = box;
         g.off[k] = (int)blocks;
         blocks += (long long)((e.d.mx + 31) / 32) * outer;
-        smem = std::max(smem, 128 + tiles + col_smem_bytes(P, sizeof(T), len, e.ln.S));
+        smem = std::max(smem, 128 + tiles + col_smem_bytes(P, sizeof(T), len, e.ln.S, SEG));
         smax = std::max(smax, e.ln.S);
     }
     if (blocks <= 0 || blocks > (1ll << 30)) return cudaErrorInvalidValue;
@@ -812,11 +828,11 @@ cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *ord
     g.n = n;
     static size_t smem_set = 48 * 1024;
     if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_col<T, P, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_col<T, P, NB, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    k_col<T, P, NB><<<(unsigned)blocks, 32 * smax, smem, s>>>(g);
+    k_col<T, P, NB, SEG><<<(unsigned)blocks, 32 * smax, smem, s>>>(g);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -825,12 +841,21 @@ template <typename T, int P>
 cudaError_t col_group_dispatch(const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s)
 {
     auto len = [&](int i) { return a[i].axis == 1 ? a[i].d.my : a[i].d.mz; };
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return len(i) > len(j); });
-    for (int k0 = 0; k0 < n; k0 += kBatch) {
-        cudaError_t e = col_group_p<T, P, kBatch>(a, maps, order.data() + k0, std::min(kBatch, n - k0), s);
-        if (e != cudaSuccess) return e;
+    for (int i = 0; i < n; ++i)
+        if (a[i].ln.seg != kSeg && a[i].ln.seg != kSegAlt) return cudaErrorInvalidValue;
+    for (int seg : {kSeg, kSegAlt}) {
+        std::vector<int> order;
+        for (int i = 0; i < n; ++i)
+            if (a[i].ln.seg == seg) order.push_back(i);
+        std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return len(i) > len(j); });
+        const int m = (int)order.size();
+        for (int k0 = 0; k0 < m; k0 += kBatch) {
+            cudaError_t e = seg == kSeg
+                                ? col_group_p<T, P, kBatch, kSeg>(a, maps, order.data() + k0, std::min(kBatch, m - k0), s)
+                                : col_group_p<T, P, kBatch, kSegAlt>(a, maps, order.data() + k0,
+                                                                     std::min(kBatch, m - k0), s);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
