@@ -76,6 +76,20 @@ def test_ricker_source_ragged_grids(ne, p, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("ne,p", [((32, 31, 30), 3), ((64, 20, 16), 3), ((33, 65, 20), 2), ((97, 130, 4), 2)])
+def test_33_row_segments(ne, p, precision):
+    """Axes with 32 s + 1 unknowns (33, 65, 97 ...) run the line solves with
+    33-row segments (one segment fewer per line); single-segment lines, ragged
+    tails on the other axes and (97 x 130 planes in FP64) the row-tiled K1
+    with the separate y sweep are covered."""
+    case = wl.ricker_case(ne=ne, p=p, tau=2e-3, steps=20, seed=8, sigma=0.05)
+    ref = oracle_wave(case, 20)
+    _, got = gpu_wave(case, 20, precision)
+    check_state(got[20], ref[20], precision, case.tau, TOL[precision] * (2 if precision == "fp64" else 1),
+                "%s %s p=%d" % (precision, ne, p))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_fused_and_tiled_rhs_agree(precision, monkeypatch):
     """The fused K1 (tile = whole y extent, y sweep inside) and the tiled K1 +
     separate y sweep compute the same step."""
