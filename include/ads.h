@@ -178,14 +178,17 @@ int ads_step(ads_sim_t *sim, int nsteps);
  * simulation, mixed devices, nsteps < 0), CUDA. */
 int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps);
 
-/* Autotuner of the K1 line tile: times every tile height K1 can take for
- * this grid (whole z-plane with the fused y sweep when it fits shared
- * memory; 8, 16, 32 or 64 rows with a separate y sweep) for trial_steps
- * steps each on the simulation itself, restores its state and step counter
- * after every trial, and keeps the fastest.  The choice is cached for the
- * process per (grid, p, precision, kind): later calls for the same shape
- * apply it without timing.  trial_steps = 0 takes the default tile.
- * *tile_rows (nullable) receives the chosen height.  Waits. */
+/* Autotuner of the K1 line tile: times every layout K1 can take for this
+ * grid (whole z-plane with the fused y sweep in one CTA when it fits shared
+ * memory; FP32 only: the z-plane split over a 2-CTA cluster, the y sweep
+ * reading the partner's rows through distributed shared memory, when two
+ * such CTAs fit one SM; 8, 16, 32 or 64 rows with a separate y sweep) for
+ * trial_steps steps each on the simulation itself, restores its state and
+ * step counter after every trial, and keeps the fastest.  The choice is
+ * cached for the process per (grid, p, precision, kind): later calls for
+ * the same shape apply it without timing.  trial_steps = 0 takes the
+ * default layout.  *tile_rows (nullable) receives the rows one CTA holds
+ * (for a cluster pair: its larger half).  Waits. */
 int ads_autotune(ads_sim_t *sim, int trial_steps, int *tile_rows);
 
 /* Wait for the simulation's stream; reports asynchronous CUDA errors. */

@@ -95,6 +95,7 @@ struct ads_sim {
     ads_source_t src{};
     // kernel tiling of K1 per precision
     int ty[2] = {0, 0}, tz[2] = {0, 0}, fuse[2] = {0, 0};
+    int pair[2] = {0, 0};   // FP32: K1 as a 2-CTA cluster per z-plane
     int seg = 32;           // register segment width of the line solves
     // graphs: chunk size -> executable graph, and the kernels it launches
     std::map<int, cudaGraphExec_t> graphs;
@@ -402,6 +403,7 @@ ads::RhsArgs<T> rhs_args(const ads_sim *s, const T *in, T *out, int set, int tof
     a.toff = toff;
     a.tau = s->tau;
     a.ty = s->ty[pi];
+    a.pair = sizeof(T) == 4 ? s->pair[pi] : 0;
     a.err = s->d_err;
     return a;
 }
@@ -1115,17 +1117,20 @@ int batch_groups(std::map<std::pair<int, int>, std::vector<ads_sim *>> &groups, 
 
 // ------------------------------------------------------------------ autotuner
 
-// Tile heights K1 can take for this simulation: the whole plane (fused y
-// sweep) when it fits the shared-memory budget, and row tiles of 8..64
-// rows with a separate y sweep.
-std::vector<int> tile_candidates(const ads_sim *s)
+// K1 layouts this simulation can take: the whole plane (fused y sweep) in
+// one CTA when it fits the shared-memory budget, the plane split over a
+// 2-CTA cluster (FP32, when two such CTAs fit an SM), and row tiles of
+// 8..64 rows with a separate y sweep.  (rows, pair)
+std::vector<std::pair<int, int>> tile_candidates(const ads_sim *s)
 {
     const int el = (int)elem(s);
     const int Sx = segs(s, s->d.mx), Sy = segs(s, s->d.my), my = s->d.my;
-    std::vector<int> c;
-    if (ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg) <= 220 * 1024) c.push_back(my);
+    std::vector<std::pair<int, int>> c;
+    if (ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg) <= 220 * 1024) c.push_back({my, 0});
+    if (el == 4 && my >= 2 && ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg, 1) <= 110 * 1024)
+        c.push_back({my, 1});
     for (int t : {8, 16, 32, 64})
-        if (t < my && ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy, s->seg) <= 220 * 1024) c.push_back(t);
+        if (t < my && ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy, s->seg) <= 220 * 1024) c.push_back({t, 0});
     return c;
 }
 
@@ -1137,18 +1142,19 @@ struct TuneKey {
     }
 };
 
-std::map<TuneKey, int> &tune_cache()
+std::map<TuneKey, std::pair<int, int>> &tune_cache()
 {
-    static std::map<TuneKey, int> c;
+    static std::map<TuneKey, std::pair<int, int>> c;
     return c;
 }
 
-void set_tile(ads_sim *s, int ty)
+void set_tile(ads_sim *s, std::pair<int, int> t)
 {
     const int pi = s->prec == ADS_FP64 ? 0 : 1;
-    if (s->ty[pi] == ty) return;
-    s->ty[pi] = ty;
-    s->fuse[pi] = ty == s->d.my;
+    if (s->ty[pi] == t.first && s->pair[pi] == t.second) return;
+    s->ty[pi] = t.first;
+    s->pair[pi] = t.second;
+    s->fuse[pi] = t.first == s->d.my;
     drop_graphs(s);
 }
 
@@ -1164,7 +1170,7 @@ int autotune(ads_sim *s, int trial_steps)
         set_tile(s, hit->second);
         return ADS_OK;
     }
-    const std::vector<int> cand = tile_candidates(s);
+    const std::vector<std::pair<int, int>> cand = tile_candidates(s);
     if (cand.empty()) return fail(ADS_ERR_UNSUPPORTED, "ads_autotune: no tile fits shared memory");
     if (cand.size() == 1 || trial_steps == 0) {
         set_tile(s, cand[0]);
@@ -1193,11 +1199,13 @@ int autotune(ads_sim *s, int trial_steps)
     cudaEvent_t e0, e1;
     ADS_CK(cudaEventCreate(&e0));
     ADS_CK(cudaEventCreate(&e1));
-    const int orig = s->ty[s->prec == ADS_FP64 ? 0 : 1];
-    int best = cand[0], rc = ADS_OK;
+    const int pi = s->prec == ADS_FP64 ? 0 : 1;
+    const std::pair<int, int> orig{s->ty[pi], s->pair[pi]};
+    std::pair<int, int> best = cand[0];
+    int rc = ADS_OK;
     float best_ms = 1e30f;
     const unsigned long long launches = ads::g_launches;
-    for (int t : cand) {
+    for (const std::pair<int, int> &t : cand) {
         set_tile(s, t);
         if ((rc = step_once(s, false))) break;
         cudaEventRecord(e0, s->stream);
@@ -1703,7 +1711,11 @@ int ads_autotune(ads_sim_t *s, int trial_steps, int *tile_rows)
     cudaSetDevice(s->device);
     int rc = autotune(s, trial_steps);
     if (rc) return rc;
-    if (tile_rows) *tile_rows = s->ty[s->prec == ADS_FP64 ? 0 : 1];
+    const int pi = s->prec == ADS_FP64 ? 0 : 1;
+    // a pair reports the rows of its larger CTA (the split is a multiple of 32)
+    int cut = ((s->d.my / 2) + 31) & ~31;
+    if (cut > s->d.my) cut = s->d.my;
+    if (tile_rows) *tile_rows = s->pair[pi] ? std::max(cut, s->d.my - cut) : s->ty[pi];
     return ADS_OK;
 }
 

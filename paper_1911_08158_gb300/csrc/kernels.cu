@@ -531,14 +531,10 @@ size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy, int seg)
            line_image_elems(p, Sy, seg);
 }
 
-size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg)
+size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg, int pair)
 {
-    const int RS = ((d.mx + 1) & ~1) | 1;
-    const int rows_pad = (ty + 31) & ~31, cols_pad = (d.mx + 31) & ~31;
-    const bool fuse = ty == d.my;
-    const int cld = (fuse && cols_pad > rows_pad) ? cols_pad : rows_pad;
-    const int Smax = (fuse && Sy > Sx) ? Sy : Sx;
-    size_t n = 2 * (size_t)ty * RS + 2 * (size_t)Smax * p * cld;
+    const RhsPlan q = rhs_plan(d.mx, d.my, ty, pair, Sx, Sy);
+    size_t n = 2 * (size_t)q.rows * q.RS + 2 * (size_t)q.Smax * p * q.cld;
     return n * elem + 16 + ((rhs_image_elems(p, d, Sx, Sy, seg) * elem + 15) & ~(size_t)15);
 }
 

@@ -75,6 +75,7 @@ struct RhsArgs {
     int ty;               // rows per tile (y); fused y sweep iff ty == my
     int *err;             // device error word (bounded waits)
     int direct;           // 1: `in` is the RHS itself (no quadrature): out = Ax^{-1} [Ay^{-1}] in
+    int pair;             // 1 (FP32): a 2-CTA cluster per z-plane (fused y sweep across the pair)
 };
 
 // Column sweep along y (axis 1) or z (axis 2): 32 x-columns per CTA, one
@@ -131,7 +132,7 @@ struct ColGroup {
 };
 
 // seg: register segment width of the partitioned solves (32)
-size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg);
+size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg, int pair = 0);
 int rhs_threads(int elem);
 // element offsets of the K1 table image: returns total elements
 size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy, int seg);

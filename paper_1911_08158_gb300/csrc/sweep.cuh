@@ -14,6 +14,7 @@
 // per-simulation ranges (RhsGroup::off / ColGroup::off), so one launch
 // advances a whole batch; NB = 1 is the single-simulation launch.
 #pragma once
+#include <cooperative_groups.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -366,9 +367,11 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
 //  3. whole plane in the tile: y-direction solve, thread per (x, segment),
 //     results stored from registers to global memory.
 //  4. row tiles only: coalesced store of S1.
-template <typename T>
+template <typename T, bool PAIR>
 struct RhsThreads {
-    static constexpr int value = sizeof(T) == 8 ? 256 : 512;   // FP64: more registers per thread
+    // FP64: more registers per thread; a pair CTA holds half a plane, two per SM
+    static constexpr int value = (sizeof(T) == 8 ? 256 : 512) / (PAIR ? 2 : 1);
+    static constexpr int per_sm = PAIR ? 2 : 1;
 };
 
 // index of the simulation that owns block b: off[i] <= b < off[i+1]
@@ -383,8 +386,9 @@ __device__ __forceinline__ int group_find(const int *off, int n, int b)
     return lo;
 }
 
-template <typename T, int P, int NB, int SEG>
-__global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_constant__ RhsGroup<T, NB> g)
+template <typename T, int P, int NB, int SEG, bool PAIR>
+__global__ void __launch_bounds__(RhsThreads<T, PAIR>::value, RhsThreads<T, PAIR>::per_sm)
+    k_rhs(const __grid_constant__ RhsGroup<T, NB> g)
 {
     const int gs = NB > 1 ? group_find(g.off, g.n, blockIdx.x) : 0;
     const RhsArgs<T> &a = g.a[gs];
@@ -394,21 +398,33 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
     __shared__ T s_r;
     const int mx = a.d.mx, my = a.d.my, mz = a.d.mz, sx = a.d.sx;
     const long long plane = (long long)sx * my;
-    const int RS = ((mx + 1) & ~1) | 1;   // odd, holds every column pair
-    const int ty = a.ty;
-    const int nty = (my + ty - 1) / ty;
-    const int y0 = (lb % nty) * ty, z = lb / nty;
-    const int tye = min(ty, my - y0);
-    const bool fuse_y = (ty == my);
+    const RhsPlan q = rhs_plan(mx, my, a.ty, PAIR ? 1 : 0, a.lx.S, a.ly.S);
+    const int RS = q.RS;   // odd, holds every column pair
+    // this CTA's rows [y0, y0 + tye) of plane z; a pair splits the plane at
+    // q.ycut (rank 0 below, rank 1 above; cluster ranks are consecutive blocks)
+    int y0, z, tye, half = 0;
+    if (PAIR) {
+        half = lb & 1;
+        z = lb >> 1;
+        y0 = half ? q.ycut : 0;
+        tye = half ? my - q.ycut : q.ycut;
+    } else {
+        const int ty = a.ty;
+        const int nty = (my + ty - 1) / ty;
+        y0 = (lb % nty) * ty;
+        z = lb / nty;
+        tye = min(ty, my - y0);
+    }
+    const bool fuse_y = q.fuse;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
-    const int rows_pad = (ty + 31) & ~31, cols_pad = (mx + 31) & ~31;
-    const int cld = (fuse_y && cols_pad > rows_pad) ? cols_pad : rows_pad;
+    const int rows_pad = (tye + 31) & ~31;
+    const int cld = q.cld;
 
     __shared__ __align__(8) uint64_t bar;
     T *S1 = reinterpret_cast<T *>(smem_raw);
-    T *S2 = S1 + (size_t)ty * RS;
-    const int Smax = (fuse_y && a.ly.S > a.lx.S) ? a.ly.S : a.lx.S;
-    T *CT = S2 + (size_t)ty * RS;
+    T *S2 = S1 + (size_t)q.rows * RS;
+    const int Smax = q.Smax;
+    T *CT = S2 + (size_t)q.rows * RS;
     T *CH = CT + (size_t)Smax * P * cld;
     // the 1D tables arrive as one bulk copy into a 16-byte aligned region
     T *tb = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(CH + (size_t)Smax * P * cld) + 15) & ~(uintptr_t)15);
@@ -493,8 +509,15 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
         }
     }
     // tables in shared memory from here on; every thread leaves together if
-    // the copy did not arrive (the error word tells the host)
-    if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, a.err))) return;
+    // the copy did not arrive (the error word tells the host); a pair CTA
+    // still meets its partner at both cluster barriers first
+    if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, a.err))) {
+        if (PAIR) {
+            cooperative_groups::this_cluster().sync();
+            cooperative_groups::this_cluster().sync();
+        }
+        return;
+    }
 
     // ---- phase 2: x-direction, thread per (row, segment); rounds of row groups
     const int RG = rows_pad >> 5;
@@ -555,19 +578,43 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
 
     // ---- phase 3: y-direction (whole plane), thread per (x, segment); rounds of column groups
     if (fuse_y) {
-        const int CG = cols_pad >> 5;
+        // a pair sweeps columns [c0, c1) over the rows of both CTAs: rows below
+        // q.ycut live in rank 0's S1, the others in rank 1's (read through
+        // distributed shared memory once both have finished phase 2)
+        int c0 = 0, c1 = mx;
+        const T *Slo = S1, *Shi = S1;
+        if (PAIR) {
+            cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+            cl.sync();
+            const T *peer = cl.map_shared_rank(S1, half ^ 1);
+            Slo = half ? peer : S1;
+            Shi = half ? S1 : peer;
+            c0 = half ? q.xcut : 0;
+            c1 = half ? mx : q.xcut;
+        }
+        const int ycut = PAIR ? q.ycut : my;
+        const int CG = (c1 - c0 + 31) >> 5;
         const int gpr3 = nwarps / LY.S > 0 ? nwarps / LY.S : 1;
         for (int g0 = 0; g0 < CG; g0 += gpr3) {
             const int gi = warp / LY.S, s = warp % LY.S;
-            const int x = (g0 + gi) * 32 + lane;
-            const bool on = gi < gpr3 && x < mx;
+            const int xl = (g0 + gi) * 32 + lane;   // column slot within this CTA's range
+            const int x = c0 + xl;
+            const bool on = gi < gpr3 && x < c1;
             const int b0 = s * SEG;
             const int n = on ? min(SEG, my - b0) : 0;
             T v[SEG];
+            if constexpr (PAIR) {
 #pragma unroll
-            for (int k = 0; k < SEG; ++k) v[k] = (k < n) ? S1[(size_t)(b0 + k) * RS + x] : T(0);
+                for (int k = 0; k < SEG; ++k) {
+                    const int r = b0 + k;
+                    v[k] = (k < n) ? (r < ycut ? Slo[(size_t)r * RS + x] : Shi[(size_t)(r - ycut) * RS + x]) : T(0);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < SEG; ++k) v[k] = (k < n) ? S1[(size_t)(b0 + k) * RS + x] : T(0);
+            }
             if (on) seg_pass1<T, P, SEG>(LY.fac + b0 * W, v);
-            seg_finish<T, P, SEG>(LY, on, s, x, cld, CT, CH, v);
+            seg_finish<T, P, SEG>(LY, on, s, xl, cld, CT, CH, v);
             // finished columns go straight to global memory (lanes = consecutive
             // x: one coalesced row segment per k); the next round reads other
             // columns of S1 and its carry writes follow seg_finish's barriers
@@ -578,6 +625,8 @@ __global__ void __launch_bounds__(RhsThreads<T>::value, 1) k_rhs(const __grid_co
                     if (k < n) dst[(long long)k * sx] = v[k];
             }
         }
+        // the partner may still be reading this CTA's S1
+        if (PAIR) cooperative_groups::this_cluster().sync();
     }
 
     // ---- phase 4: store (row tiles; the fused path stored in phase 3)
@@ -725,11 +774,11 @@ bool rhs_entry_ok(const RhsArgs<T> &a, int seg)
 template <typename T>
 int rhs_blocks(const RhsArgs<T> &a)
 {
-    return (a.d.my + a.ty - 1) / a.ty * a.d.mz;
+    return a.pair ? 2 * a.d.mz : (a.d.my + a.ty - 1) / a.ty * a.d.mz;
 }
 
 // one launch of up to NB simulations, entries a[order[0..n)]
-template <typename T, int P, int NB, int SEG>
+template <typename T, int P, int NB, int SEG, bool PAIR>
 cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream_t s)
 {
     RhsGroup<T, NB> g;
@@ -738,51 +787,82 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
     long long blocks = 0;
     for (int k = 0; k < n; ++k) {
         const RhsArgs<T> &e = a[order[k]];
-        if (!rhs_entry_ok(e, SEG)) return cudaErrorInvalidValue;
+        if (!rhs_entry_ok(e, SEG) || (e.pair != 0) != PAIR) return cudaErrorInvalidValue;
         g.a[k] = e;
         g.off[k] = (int)blocks;
         blocks += rhs_blocks(e);
-        smem = std::max(smem, rhs_smem_bytes(P, sizeof(T), e.d, e.ty, e.lx.S, e.ly.S, SEG));
+        smem = std::max(smem, rhs_smem_bytes(P, sizeof(T), e.d, e.ty, e.lx.S, e.ly.S, SEG, PAIR ? 1 : 0));
     }
     if (blocks <= 0 || blocks > (1ll << 30)) return cudaErrorInvalidValue;
     g.off[n] = (int)blocks;
     g.n = n;
     static size_t smem_set = 48 * 1024;   // per instantiation: opt-in dynamic shared memory
     if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rhs<T, P, NB, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_rhs<T, P, NB, SEG, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    k_rhs<T, P, NB, SEG><<<(unsigned)blocks, RhsThreads<T>::value, smem, s>>>(g);
     ++g_launches;
-    return cudaGetLastError();
+    if (!PAIR) {
+        k_rhs<T, P, NB, SEG, PAIR><<<(unsigned)blocks, RhsThreads<T, PAIR>::value, smem, s>>>(g);
+        return cudaGetLastError();
+    }
+    // two CTAs per cluster: the halves of one z-plane (every simulation's
+    // block range has an even length, so clusters never straddle two)
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+    cfg.blockDim = dim3(RhsThreads<T, PAIR>::value, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_rhs<T, P, NB, SEG, PAIR>, g);
 }
 
-// A single simulation is a group of one: one instantiation per (T, P)
-// serves both (its parameters are read with a run-time index, which keeps
-// them out of the register budget of the sweeps).
+// A single simulation is a group of one: one instantiation per (T, P, SEG,
+// pairing) serves both (its parameters are read with a run-time index, which
+// keeps them out of the register budget of the sweeps).  Pairs are FP32 only.
 template <typename T, int P>
 cudaError_t rhs_group_dispatch(const RhsArgs<T> *a, int n, cudaStream_t s)
 {
-    // heaviest blocks first (rows x columns of a tile) so that the tail of
-    // the launch holds the short ones
     for (int i = 0; i < n; ++i)
-        if (a[i].lx.seg != kSeg && a[i].lx.seg != kSegAlt) return cudaErrorInvalidValue;
-    for (int seg : {kSeg, kSegAlt}) {
-        std::vector<int> order;
-        for (int i = 0; i < n; ++i)
-            if (a[i].lx.seg == seg) order.push_back(i);
-        std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
-            return (long long)a[i].ty * a[i].d.mx > (long long)a[j].ty * a[j].d.mx;
-        });
-        const int m = (int)order.size();
-        for (int k0 = 0; k0 < m; k0 += kBatch) {
-            cudaError_t e = seg == kSeg ? rhs_group_p<T, P, kBatch, kSeg>(a, order.data() + k0, std::min(kBatch, m - k0), s)
-                                        : rhs_group_p<T, P, kBatch, kSegAlt>(a, order.data() + k0,
-                                                                             std::min(kBatch, m - k0), s);
-            if (e != cudaSuccess) return e;
+        if ((a[i].lx.seg != kSeg && a[i].lx.seg != kSegAlt) || (a[i].pair && sizeof(T) != 4))
+            return cudaErrorInvalidValue;
+    for (int pair = 0; pair < 2; ++pair)
+        for (int seg : {kSeg, kSegAlt}) {
+            std::vector<int> order;
+            for (int i = 0; i < n; ++i)
+                if (a[i].lx.seg == seg && (a[i].pair != 0) == (pair != 0)) order.push_back(i);
+            // heaviest blocks first (rows x columns of a tile) so that the tail of
+            // the launch holds the short ones
+            auto cost = [&](int i) {
+                const int rows = a[i].pair ? (a[i].d.my + 1) / 2 : a[i].ty;
+                return (long long)rows * a[i].d.mx;
+            };
+            std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return cost(i) > cost(j); });
+            const int m = (int)order.size();
+            for (int k0 = 0; k0 < m; k0 += kBatch) {
+                const int c = std::min(kBatch, m - k0);
+                const int *o = order.data() + k0;
+                cudaError_t e = cudaSuccess;
+                if (pair) {
+                    if constexpr (sizeof(T) == 4)
+                        e = seg == kSeg ? rhs_group_p<T, P, kBatch, kSeg, true>(a, o, c, s)
+                                        : rhs_group_p<T, P, kBatch, kSegAlt, true>(a, o, c, s);
+                } else {
+                    e = seg == kSeg ? rhs_group_p<T, P, kBatch, kSeg, false>(a, o, c, s)
+                                    : rhs_group_p<T, P, kBatch, kSegAlt, false>(a, o, c, s);
+                }
+                if (e != cudaSuccess) return e;
+            }
         }
-    }
     return cudaSuccess;
 }
 
