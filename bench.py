@@ -67,7 +67,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -80,7 +80,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -209,12 +209,14 @@ def run_ours(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / dur / 1e9
-    traffic = None
+    traffic = None   # ncu DRAM bytes per launch, from the committed summary of this kernel and workload
     try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-        ent = prof.get(dom)
-        if ent and ent.get("workload") == WORKLOAD:
-            traffic = ent.get("bytes_per_launch")
+        import glob
+        for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+            for line in open(path):
+                f = line.split()
+                if len(f) == 4 and f[0] == "traffic_bytes_per_launch" and f[1] == dom and f[2] == WORKLOAD:
+                    traffic = int(f[3])
     except Exception:
         pass
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -456,8 +458,9 @@ def run_reference(args):
 
 def profile_case(ne, p: int, steps: int, batch: int = 1):
     """Small fixed case for ncu captures: `batch` FP32 simulations of ne
-    (n or nx,ny,nz) elements advanced together (grouped launches; no
-    timing): two warm-up steps, then `steps` single steps."""
+    (n or nx,ny,nz) elements with autotuned K1 layouts, advanced together
+    (grouped launches; no timing): two warm-up steps, then `steps` single
+    steps."""
     import torch
 
     import paper_1911_08158_gb300 as ads
@@ -470,6 +473,7 @@ def profile_case(ne, p: int, steps: int, batch: int = 1):
         sim = ads.Simulation(case.n_elem, case.p, case.tau, precision="fp32")
         sim.set_source(case.source)
         sim.set_gaussian_state(None, None)
+        sim.autotune(3)   # the layout the benchmark would use
         sims.append(sim)
     ads.batch_step(sims, 2)
     for _ in range(steps):
