@@ -57,6 +57,8 @@ def lib():
             L.ora_mats1d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, _D]
             L.ora_space_new.argtypes = [_I, ctypes.c_int, _D]
             L.ora_space_new.restype = ctypes.c_void_p
+            L.ora_space_new_bc.argtypes = [_I, ctypes.c_int, _D, ctypes.c_int]
+            L.ora_space_new_bc.restype = ctypes.c_void_p
             L.ora_space_free.argtypes = [ctypes.c_void_p]
             L.ora_space_dims.argtypes = [ctypes.c_void_p, _I]
             L.ora_space_mat.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D]
@@ -144,15 +146,18 @@ def num_threads() -> int:
 
 # ---------------------------------------------------------------- 3D space
 class Space:
-    """Tensor-product spline space on [0,L]^3 with Dirichlet restriction."""
+    """Tensor-product spline space on [0,L]^3: homogeneous Dirichlet
+    restriction (first and last function per axis dropped), or, with
+    natural=True, every basis function kept (traction-free / natural
+    boundary)."""
 
-    def __init__(self, ne, p: int, L=(1.0, 1.0, 1.0)):
+    def __init__(self, ne, p: int, L=(1.0, 1.0, 1.0), natural: bool = False):
         ne = tuple(int(v) for v in (ne if np.ndim(ne) else (ne, ne, ne)))
         L = tuple(float(v) for v in (L if np.ndim(L) else (L, L, L)))
-        self.ne, self.p, self.L = ne, int(p), L
+        self.ne, self.p, self.L, self.natural = ne, int(p), L, bool(natural)
         nea = (ctypes.c_int * 3)(*ne)
         La = (ctypes.c_double * 3)(*L)
-        self._h = lib().ora_space_new(nea, self.p, La)
+        self._h = lib().ora_space_new_bc(nea, self.p, La, int(self.natural))
         m = (ctypes.c_int * 3)()
         lib().ora_space_dims(self._h, m)
         self.m = (m[0], m[1], m[2])                 # (mx, my, mz)
@@ -287,12 +292,17 @@ class Space:
 
     # ---- layout helpers
     def pad(self, a):
-        """Interior (.., mz, my, mx) -> full (.., nz, ny, nx) with zero boundary."""
+        """Unknowns (.., mz, my, mx) -> full (.., nz, ny, nx): zero boundary
+        coefficients (Dirichlet), or the same array (natural boundary)."""
         a = np.asarray(a)
+        if self.natural:
+            return np.array(a, dtype=np.float64)
         out = np.zeros(a.shape[:-3] + (self.n[2], self.n[1], self.n[0]))
         out[..., 1:-1, 1:-1, 1:-1] = a
         return out
 
-    @staticmethod
-    def interior(a):
+    def interior(self, a):
+        """Full coefficient array -> the unknowns (inverse of pad)."""
+        if self.natural:
+            return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
         return np.ascontiguousarray(np.asarray(a)[..., 1:-1, 1:-1, 1:-1])

@@ -170,17 +170,22 @@ void ora_mats1d(int ne, int p, double L, double *M, double *K, double *B)
 
 typedef struct {
     int ne[3], p, n[3], m[3];
+    int off;                      /* 1: Dirichlet (first/last function dropped), 0: natural */
     double L[3];
     double *M[3], *K[3], *B[3];   /* restricted m x m, row-major */
     double *t[3];                 /* knot vectors */
 } ora_space;
 
-ora_space *ora_space_new(const int *ne, int p, const double *L)
+/* natural != 0 keeps every basis function (traction-free / natural boundary,
+ * Sec. 5); otherwise the homogeneous Dirichlet restriction drops the first
+ * and last function per axis. */
+ora_space *ora_space_new_bc(const int *ne, int p, const double *L, int natural)
 {
     ora_space *s = (ora_space *)calloc(1, sizeof(ora_space));
     s->p = p;
+    s->off = natural ? 0 : 1;
     for (int a = 0; a < 3; a++) {
-        int n = ne[a] + p, m = n - 2;
+        int n = ne[a] + p, m = n - 2 * s->off;
         s->ne[a] = ne[a];
         s->n[a] = n;
         s->m[a] = m;
@@ -193,11 +198,12 @@ ora_space *ora_space_new(const int *ne, int p, const double *L)
         s->K[a] = (double *)malloc(sizeof(double) * (size_t)m * m);
         s->B[a] = (double *)malloc(sizeof(double) * (size_t)m * m);
         /* Dirichlet: drop basis functions 0 and n-1 */
+        const int o = s->off;
         for (int i = 0; i < m; i++)
             for (int j = 0; j < m; j++) {
-                s->M[a][i * m + j] = Mf[(i + 1) * n + (j + 1)];
-                s->K[a][i * m + j] = Kf[(i + 1) * n + (j + 1)];
-                s->B[a][i * m + j] = Bf[(i + 1) * n + (j + 1)];
+                s->M[a][i * m + j] = Mf[(i + o) * n + (j + o)];
+                s->K[a][i * m + j] = Kf[(i + o) * n + (j + o)];
+                s->B[a][i * m + j] = Bf[(i + o) * n + (j + o)];
             }
         free(Mf); free(Kf); free(Bf);
         s->t[a] = (double *)malloc(sizeof(double) * (size_t)(ne[a] + 2 * p + 1));
@@ -205,6 +211,8 @@ ora_space *ora_space_new(const int *ne, int p, const double *L)
     }
     return s;
 }
+
+ora_space *ora_space_new(const int *ne, int p, const double *L) { return ora_space_new_bc(ne, p, L, 0); }
 
 void ora_space_free(ora_space *s)
 {
@@ -411,15 +419,15 @@ void ora_load_gauss(const ora_space *s, double amp, const double *c, double den,
                             double g = amp * exp(-(dx * dx + dy * dy + dz * dz) / den);
                             double w = W[0][ix] * W[1][iy] * W[2][iz] * g;
                             for (int bz = 0; bz <= p; bz++) {
-                                int k = ez + bz - 1;          /* interior index */
+                                int k = ez + bz - s->off;     /* unknown index */
                                 if (k < 0 || k >= s->m[2]) continue;
                                 double vz = V[2][iz * (p + 1) + bz];
                                 for (int by = 0; by <= p; by++) {
-                                    int j = ey + by - 1;
+                                    int j = ey + by - s->off;
                                     if (j < 0 || j >= my) continue;
                                     double vy = V[1][iy * (p + 1) + by];
                                     for (int bx = 0; bx <= p; bx++) {
-                                        int i = ex + bx - 1;
+                                        int i = ex + bx - s->off;
                                         if (i < 0 || i >= mx) continue;
                                         double vx = V[0][ix * (p + 1) + bx];
                                         out[((size_t)k * my + j) * mx + i] += w * vx * vy * vz;

@@ -73,14 +73,16 @@ def tables(ne, p, L=1.0):
     return V, D, W
 
 
-def elastic_dense(ne, p, lam, mu, L=(1.0, 1.0, 1.0)):
-    """Dense elasticity stiffness on the interior DOFs, assembled by direct 3D
-    quadrature of  mu (d_ab grad phi_A . grad phi_B + d_b phi_A d_a phi_B)
+def elastic_dense(ne, p, lam, mu, L=(1.0, 1.0, 1.0), natural=False):
+    """Dense elasticity stiffness on the unknowns (interior DOFs with the
+    Dirichlet restriction, every DOF with natural=True), assembled by direct
+    3D quadrature of  mu (d_ab grad phi_A . grad phi_B + d_b phi_A d_a phi_B)
     + lam d_a phi_A d_b phi_B  (the bilinear form 2mu e(w):e(u) + lam div w div u
     for w = phi_A e_a, u = phi_B e_b).  Component-major, x fastest."""
     T = [tables(ne[a], p, L[a]) for a in range(3)]
     n = [ne[a] + p for a in range(3)]
-    m = [v - 2 for v in n]
+    off = 0 if natural else 1
+    m = [v - 2 * off for v in n]
     N = m[0] * m[1] * m[2]
     S = np.zeros((3 * N, 3 * N))
     q = p + 1
@@ -92,7 +94,7 @@ def elastic_dense(ne, p, lam, mu, L=(1.0, 1.0, 1.0)):
                 for bz in range(q):
                     for by in range(q):
                         for bx in range(q):
-                            i, j, k = ex + bx - 1, ey + by - 1, ez + bz - 1
+                            i, j, k = ex + bx - off, ey + by - off, ez + bz - off
                             ok = 0 <= i < m[0] and 0 <= j < m[1] and 0 <= k < m[2]
                             idx.append((k * m[1] + j) * m[0] + i if ok else -1)
                 idx = np.array(idx)
