@@ -70,7 +70,15 @@ typedef struct ads_sim ads_sim_t;     /* opaque, library-owned */
 typedef struct {
     int n_elem[3];        /* elements along x, y, z (>= 1) */
     double length[3];     /* domain extents (> 0) */
+    int boundary;         /* ADS_DIRICHLET: homogeneous Dirichlet, the first and
+                             last B-spline per axis are dropped (n_elem + p - 2
+                             unknowns per axis, full arrays carry zero boundary
+                             coefficients); ADS_NATURAL: traction-free / natural
+                             boundary (Sec. 5), every B-spline is an unknown
+                             (n_elem + p per axis, full array = unknowns) */
 } ads_grid_t;
+
+enum { ADS_DIRICHLET = 0, ADS_NATURAL = 1 };
 
 typedef struct {
     int kind;             /* ADS_SCALAR_WAVE or ADS_ELASTIC */

@@ -20,6 +20,8 @@ ADS_SCALAR_WAVE, ADS_ELASTIC = 0, 1
 ADS_FP64, ADS_FP32 = 0, 1
 ADS_HOST, ADS_DEVICE = 0, 1
 ADS_OP_MASS, ADS_OP_STIFF, ADS_OP_MASS_SOLVE, ADS_OP_SPLIT_SOLVE = 0, 1, 2, 3
+ADS_DIRICHLET, ADS_NATURAL = 0, 1
+_BOUNDARY = {"dirichlet": ADS_DIRICHLET, "natural": ADS_NATURAL}
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libads_gb300.so")
 
@@ -31,7 +33,7 @@ class AdsError(RuntimeError):
 
 
 class Grid(ctypes.Structure):
-    _fields_ = [("n_elem", ctypes.c_int * 3), ("length", ctypes.c_double * 3)]
+    _fields_ = [("n_elem", ctypes.c_int * 3), ("length", ctypes.c_double * 3), ("boundary", ctypes.c_int)]
 
 
 class Material(ctypes.Structure):
@@ -177,11 +179,12 @@ class Simulation:
     def __init__(self, n_elem, p: int, tau: float, kind: str = "wave", c2: float = 1.0, lam: float = 1.0,
                  mu: float = 1.0, rho: float = 1.0, length=(1.0, 1.0, 1.0), precision: str = "fp64",
                  device: int = 0, use_torch: bool = True, stream=None, tile_lines: int = 0,
-                 residual_correction: bool = False):
+                 residual_correction: bool = False, boundary: str = "dirichlet"):
         L = library()
         ne = tuple(int(v) for v in (n_elem if np.ndim(n_elem) else (n_elem,) * 3))
         ln = tuple(float(v) for v in (length if np.ndim(length) else (length,) * 3))
-        self._grid = Grid((ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(*ln))
+        self._grid = Grid((ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(*ln), _BOUNDARY[boundary])
+        self.boundary = boundary
         k = {"wave": ADS_SCALAR_WAVE, "elastic": ADS_ELASTIC}[kind]
         self._mat = Material(k, c2, lam, mu, rho)
         prec = {"fp64": ADS_FP64, "fp32": ADS_FP32}[precision]
@@ -352,10 +355,10 @@ def selftest_timeout(device: int = 0, cycles: int = 20_000_000) -> int:
     return int(library().ads_selftest_timeout(int(device), int(cycles)))
 
 
-def estimate_bytes(n_elem, p: int, kind: str = "wave", precision: str = "fp32") -> int:
+def estimate_bytes(n_elem, p: int, kind: str = "wave", precision: str = "fp32", boundary: str = "dirichlet") -> int:
     """Device bytes a simulation of this shape will hold (ads_estimate_bytes)."""
     ne = tuple(int(v) for v in (n_elem if np.ndim(n_elem) else (n_elem,) * 3))
-    g = Grid((ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(1.0, 1.0, 1.0))
+    g = Grid((ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(1.0, 1.0, 1.0), _BOUNDARY[boundary])
     k = {"wave": ADS_SCALAR_WAVE, "elastic": ADS_ELASTIC}[kind]
     prec = {"fp64": ADS_FP64, "fp32": ADS_FP32}[precision]
     return int(library().ads_estimate_bytes(ctypes.byref(g), int(p), k, prec))

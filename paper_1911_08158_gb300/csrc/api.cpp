@@ -59,6 +59,7 @@ enum { IMG_EL = NSETS, NIMG = NSETS + 3 };
 // Device copy of a set of FP64 host tables in precision T.
 struct TableSet {
     void *M[3] = {}, *K[3] = {}, *B[3] = {};   // operator bands [m_pad][2p+1]
+    void *Bt[3] = {};                          // B^T bands (natural boundary)
     LineTables line[NSETS][3];                 // per factor set and axis
     void *img[NIMG] = {};                      // K1 images (x and y tables of a set)
     int img_bytes[NIMG] = {};
@@ -313,6 +314,7 @@ int build_tables(ads_sim *s, TableSet &ts)
         if ((rc = upload<T>(s, s->hM[a], &ts.M[a]))) return rc;
         if ((rc = upload<T>(s, s->hK[a], &ts.K[a]))) return rc;
         if ((rc = upload<T>(s, pad_rows(ax.B.v, ax.m, W, mp, false), &ts.B[a]))) return rc;
+        if (s->d.off == 0 && (rc = upload<T>(s, pad_rows(ax.Bt.v, ax.m, W, mp, false), &ts.Bt[a]))) return rc;
         for (int set = 0; set < NSETS; ++set)
             if (!s->hline[set][a].empty() && (rc = upload_line<T>(s, set, a, &ts.line[set][a]))) return rc;
         if (s->kind == ADS_SCALAR_WAVE) {
@@ -518,7 +520,8 @@ int check_device_error(ads_sim *s)
 
 size_t full_count(const ads_sim *s)
 {
-    return (size_t)(s->d.mx + 2) * (s->d.my + 2) * (s->d.mz + 2) * (s->kind == ADS_ELASTIC ? 3 : 1);
+    const int o = 2 * s->d.off;
+    return (size_t)(s->d.mx + o) * (s->d.my + o) * (s->d.mz + o) * (s->kind == ADS_ELASTIC ? 3 : 1);
 }
 
 // a = M^{-1}(F(t_n) - K u) for an FP64 interior u
@@ -696,7 +699,8 @@ int kron3(ads_sim *s, const T *in, T *out, const int *which, T coef, bool accumu
 {
     const TableSet &ts = tables_for<T>(s);
     const void *band[3];
-    for (int a = 0; a < 3; ++a) band[a] = which[a] == 0 ? ts.M[a] : (which[a] == 1 ? ts.K[a] : ts.B[a]);
+    for (int a = 0; a < 3; ++a)
+        band[a] = which[a] == 0 ? ts.M[a] : (which[a] == 1 ? ts.K[a] : (which[a] == 2 ? ts.B[a] : ts.Bt[a]));
     (void)ta;
     (void)tb;
     ADS_CK(ads::launch_kron3<T>(s->p, (const T *)band[0], (const T *)band[1], (const T *)band[2], in, out, s->d, coef,
@@ -710,7 +714,8 @@ ads::KronTerm<T> kterm(const ads_sim *s, const int *which, const T *in, T coef)
 {
     const TableSet &ts = tables_for<T>(s);
     const void *band[3];
-    for (int a = 0; a < 3; ++a) band[a] = which[a] == 0 ? ts.M[a] : (which[a] == 1 ? ts.K[a] : ts.B[a]);
+    for (int a = 0; a < 3; ++a)
+        band[a] = which[a] == 0 ? ts.M[a] : (which[a] == 1 ? ts.K[a] : (which[a] == 2 ? ts.B[a] : ts.Bt[a]));
     ads::KronTerm<T> t{};
     t.bx = (const T *)band[0];
     t.by = (const T *)band[1];
@@ -730,16 +735,42 @@ ads::KronTerm<T> plain_term(const T *in, T coef)
     return t;
 }
 
+// a full term list marks the sum invalid (nt = -1): the launch then fails
 template <typename T>
 void add_term(ads::KronSum<T> &ks, const ads::KronTerm<T> &t)
 {
+    if (ks.nt < 0 || ks.nt >= ads::kMaxKronTerms) {
+        ks.nt = -1;
+        return;
+    }
     ks.t[ks.nt++] = t;
+}
+
+// Off-diagonal block Ups_ij (i != j) as Kronecker terms scaled by coef:
+//   mu [B^T on axis i, B on axis j] + lam [B on axis i, B^T on axis j]  (M on the third);
+// with the Dirichlet restriction B^T = -B, so this is -(mu + lam) [B_i B_j]
+// (one term).
+template <typename T>
+void add_offdiag(const ads_sim *s, ads::KronSum<T> &ks, int i, int j, const T *in, double coef)
+{
+    int b[3] = {0, 0, 0};
+    if (s->d.off == 1) {
+        b[i] = 2;
+        b[j] = 2;
+        add_term(ks, kterm<T>(s, b, in, (T)(-coef * (s->lam + s->mu))));
+        return;
+    }
+    b[i] = 3;
+    b[j] = 2;
+    add_term(ks, kterm<T>(s, b, in, (T)(coef * s->mu)));
+    b[i] = 2;
+    b[j] = 3;
+    add_term(ks, kterm<T>(s, b, in, (T)(coef * s->lam)));
 }
 
 // out_i = coef (Ups U)_i, i = 0..2 (component stride cnt), one launch per
 // component:  (Ups U)_i = sum_a c_ia (K on axis a, M elsewhere) U_i
-//                         - (mu + lam) sum_{j != i} (B on axes i, j) U_j,
-// c_ia = mu + (mu + lam) [a == i]
+//                         + sum_{j != i} Ups_ij U_j,   c_ia = mu + (mu + lam) [a == i]
 template <typename T>
 int apply_upsilon(ads_sim *s, const T *U, T *out, T *ta, T *tb, T coef = T(1))
 {
@@ -754,13 +785,8 @@ int apply_upsilon(ads_sim *s, const T *U, T *out, T *ta, T *tb, T coef = T(1))
             w[a] = 1;
             add_term(ks, kterm<T>(s, w, U + i * cnt, (T)(coef * (s->mu + (a == i ? lm : 0.0)))));
         }
-        for (int j = 0; j < 3; ++j) {
-            if (j == i) continue;
-            int b[3] = {0, 0, 0};
-            b[i] = 2;
-            b[j] = 2;
-            add_term(ks, kterm<T>(s, b, U + j * cnt, (T)(-coef * lm)));
-        }
+        for (int j = 0; j < 3; ++j)
+            if (j != i) add_offdiag<T>(s, ks, i, j, U + j * cnt, (double)coef);
         ADS_CK(ads::launch_kron_sum<T>(s->p, ks, out + i * cnt, s->d, s->stream));
     }
     return ADS_OK;
@@ -825,43 +851,29 @@ int elastic_step(ads_sim *s, KernelTimer *kt = nullptr)
     const long long cnt = s->d.count();
     T *U = (T *)s->U, *Up = (T *)s->Up, *R = (T *)s->R, *Y = (T *)s->Y;
     const T tau2 = (T)(s->tau * s->tau), rho = (T)s->rho;
-    const T half = (T)(0.5 * s->tau * s->tau * (s->lam + s->mu) / s->rho);   // (1/2) tau^2 (mu+lam) / rho
     int rc;
-    auto bb = [](int i, int j, int *b) {
-        b[0] = b[1] = b[2] = 0;
-        b[i] = 2;
-        b[j] = 2;
-    };
     if (kt && (rc = kt->mark(s->stream, "elastic_rhs"))) return rc;
     // R = tau^2 (f^n - Ups U^n)
     if ((rc = apply_upsilon<T>(s, U, R, nullptr, nullptr, -tau2))) return rc;
     if ((rc = add_body_force<T>(s, R, s->tau * s->tau, 0))) return rc;
     if (kt && (rc = kt->mark(s->stream, "elastic_lower"))) return rc;
-    // lower: y_i = L~_i^{-1} (R_i / rho + (tau^2/2)(mu+lam)/rho sum_{j<i} [B_i B_j M] y_j)
-    //        (-Ups_ij = (mu+lam) [B_i B_j M] with the Dirichlet restriction)
+    // lower: y_i = L~_i^{-1} (R_i / rho - tau^2/(2 rho) sum_{j<i} Ups_ij y_j)
+    const double hr = 0.5 * s->tau * s->tau / s->rho;
     for (int i = 0; i < 3; ++i) {
         ads::KronSum<T> ks{};
         add_term(ks, plain_term<T>(R + i * cnt, T(1) / rho));
-        for (int j = 0; j < i; ++j) {
-            int b[3];
-            bb(i, j, b);
-            add_term(ks, kterm<T>(s, b, Y + j * cnt, half));
-        }
+        for (int j = 0; j < i; ++j) add_offdiag<T>(s, ks, i, j, Y + j * cnt, -hr);
         ADS_CK(ads::launch_kron_sum<T>(s->p, ks, Y + i * cnt, s->d, s->stream));
         if ((rc = elastic_diag_solve<T>(s, i, Y + i * cnt))) return rc;
     }
     if (kt && (rc = kt->mark(s->stream, "elastic_upper"))) return rc;
-    // rho M y, then upper: delta_i = L~_i^{-1} (M y_i + half sum_{j>i} [B_i B_j M] delta_j),
+    // rho M y, then upper: delta_i = L~_i^{-1} (M y_i - tau^2/(2 rho) sum_{j>i} Ups_ij delta_j),
     // delta stored in R
     for (int i = 2; i >= 0; --i) {
         ads::KronSum<T> ks{};
         const int m3[3] = {0, 0, 0};
         add_term(ks, kterm<T>(s, m3, Y + i * cnt, T(1)));
-        for (int j = i + 1; j < 3; ++j) {
-            int b[3];
-            bb(i, j, b);
-            add_term(ks, kterm<T>(s, b, R + j * cnt, half));
-        }
+        for (int j = i + 1; j < 3; ++j) add_offdiag<T>(s, ks, i, j, R + j * cnt, -hr);
         ADS_CK(ads::launch_kron_sum<T>(s->p, ks, R + i * cnt, s->d, s->stream));
         if ((rc = elastic_diag_solve<T>(s, i, R + i * cnt))) return rc;
     }
@@ -1267,19 +1279,15 @@ int elastic_energy(ads_sim *s, double *kinetic, double *potential, double *kin_m
     if (kinetic) *kinetic = 0.5 * s->rho * vmv;
     if (potential) *potential = 0.5 * uuu;
     if (!kin_mod) return ADS_OK;
-    // w = L^T v: rho (x)(M + d K) v_i  - tau^2/2 (mu+lam) sum_{j>i} [B_i B_j M] v_j
-    const double half = 0.5 * s->tau * s->tau * (s->lam + s->mu);
+    // w = L^T v: rho (x)(M + d K) v_i + tau^2/2 sum_{j>i} Ups_ij v_j
     for (int i = 0; i < 3; ++i) {
         void *eb[3];
         for (int a = 0; a < 3; ++a) eb[a] = s->ebandFP64[a][a == i ? 0 : 1];
         if ((rc = apply_kron64(s, eb, v + i * cnt, w + i * cnt, t1))) return rc;
-        ADS_CK(ads::launch_lincomb<double>(w + i * cnt, s->rho, w + i * cnt, 0.0, nullptr, cnt, s->stream));
-        for (int j = i + 1; j < 3; ++j) {
-            int b[3] = {0, 0, 0};
-            b[i] = 2;
-            b[j] = 2;
-            if ((rc = kron3<double>(s, v + j * cnt, w + i * cnt, b, -half, true, t1, t2))) return rc;
-        }
+        ads::KronSum<double> ks{};
+        ks.beta = s->rho;
+        for (int j = i + 1; j < 3; ++j) add_offdiag<double>(s, ks, i, j, v + j * cnt, 0.5 * s->tau * s->tau);
+        ADS_CK(ads::launch_kron_sum<double>(s->p, ks, w + i * cnt, s->d, s->stream));
     }
     // z = (rho M)^{-1} w
     ADS_CK(cudaMemcpyAsync(z, w, b3, cudaMemcpyDeviceToDevice, s->stream));
@@ -1316,11 +1324,15 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     if (mat->kind == ADS_SCALAR_WAVE && !(mat->c2 > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_create: c2 must be > 0");
     if (mat->kind == ADS_ELASTIC && !(mat->mu > 0.0 && mat->rho > 0.0 && mat->lambda >= 0.0))
         return fail(ADS_ERR_INVALID_ARG, "ads_create: elasticity needs mu > 0, rho > 0, lambda >= 0");
+    if (grid->boundary != ADS_DIRICHLET && grid->boundary != ADS_NATURAL)
+        return fail(ADS_ERR_INVALID_ARG, "ads_create: boundary must be ADS_DIRICHLET or ADS_NATURAL");
+    const int drop = grid->boundary == ADS_NATURAL ? 0 : 2;
     for (int a = 0; a < 3; ++a) {
         if (grid->n_elem[a] < 1) return fail(ADS_ERR_INVALID_ARG, "ads_create: n_elem must be >= 1");
         if (!(grid->length[a] > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_create: length must be > 0");
-        if (grid->n_elem[a] + p - 2 < 1) return fail(ADS_ERR_INVALID_ARG, "ads_create: no interior basis function");
-        if (grid->n_elem[a] + p - 2 > 512) return fail(ADS_ERR_UNSUPPORTED, "ads_create: more than 512 unknowns per axis");
+        if (grid->n_elem[a] + p - drop < 1) return fail(ADS_ERR_INVALID_ARG, "ads_create: no interior basis function");
+        if (grid->n_elem[a] + p - drop > 512)
+            return fail(ADS_ERR_UNSUPPORTED, "ads_create: more than 512 unknowns per axis");
     }
     ads_options_t o{};
     o.precision = ADS_FP64;
@@ -1365,7 +1377,8 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
         s->own_stream = true;
     }
     try {
-        for (int a = 0; a < 3; ++a) s->ax[a] = ads::build_axis(grid->n_elem[a], p, grid->length[a]);
+        for (int a = 0; a < 3; ++a)
+            s->ax[a] = ads::build_axis(grid->n_elem[a], p, grid->length[a], grid->boundary == ADS_NATURAL);
     } catch (const std::exception &e) {
         ads_destroy(s);
         return fail(ADS_ERR_INVALID_ARG, e.what());
@@ -1374,6 +1387,7 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     s->d.my = s->ax[1].m;
     s->d.mz = s->ax[2].m;
     s->d.sx = (s->d.mx + 7) / 8 * 8;
+    s->d.off = grid->boundary == ADS_NATURAL ? 0 : 1;
     {
         const int m3[3] = {s->d.mx, s->d.my, s->d.mz};
         s->seg = ads::choose_seg(m3);   // 33-row segments when they save segments (m = 32 s + 1)
@@ -1465,9 +1479,9 @@ int ads_dims(const ads_sim_t *s, int *n, int *comps)
 {
     if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_dims: null sim");
     if (n) {
-        n[0] = s->d.mx + 2;
-        n[1] = s->d.my + 2;
-        n[2] = s->d.mz + 2;
+        n[0] = s->d.mx + 2 * s->d.off;
+        n[1] = s->d.my + 2 * s->d.off;
+        n[2] = s->d.mz + 2 * s->d.off;
     }
     if (comps) *comps = s->kind == ADS_ELASTIC ? 3 : 1;
     return ADS_OK;
@@ -1761,7 +1775,7 @@ int ads_energy(ads_sim_t *s, double *kinetic, double *potential, double *kin_mod
 int ads_apply(ads_sim_t *s, int op, const double *in, double *out, size_t count, int mem)
 {
     if (!s || !in || !out) return fail(ADS_ERR_INVALID_ARG, "ads_apply: null argument");
-    const size_t nf = (size_t)(s->d.mx + 2) * (s->d.my + 2) * (s->d.mz + 2);
+    const size_t nf = full_count(s) / (s->kind == ADS_ELASTIC ? 3 : 1);
     if (count != nf) return fail(ADS_ERR_INVALID_ARG, "ads_apply: count must be n0*n1*n2");
     if (mem != ADS_HOST && mem != ADS_DEVICE) return fail(ADS_ERR_INVALID_ARG, "ads_apply: mem");
     if (op == ADS_OP_SPLIT_SOLVE && s->kind != ADS_SCALAR_WAVE)
@@ -1856,7 +1870,7 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
     size_t m[3], mp[3], S[3];
     int mi[3];
     for (int a = 0; a < 3; ++a) {
-        const long long me = (long long)grid->n_elem[a] + p - 2;
+        const long long me = (long long)grid->n_elem[a] + p - (grid->boundary == ADS_NATURAL ? 0 : 2);
         if (grid->n_elem[a] < 1 || me < 1 || me > (1 << 20)) return 0;
         m[a] = (size_t)me;
         mi[a] = (int)me;
@@ -1884,6 +1898,7 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
         const size_t e = t == 0 ? 8 : 4;
         for (int a = 0; a < 3; ++a) {
             add(3 * mp[a] * W * e + 64);                                    // M, K, B
+            if (grid->boundary == ADS_NATURAL) add(mp[a] * W * e);          // B^T
             for (int k = 0; k < nsets; ++k) add(ads::line_image_elems(p, (int)S[a], seg) * e + 64);
             add(mp[a] * W * e);                                             // bands of M + eta K
             add(mp[a] * e);                                                 // source load vector
@@ -1908,7 +1923,7 @@ int ads_internal_apply_scratch(ads_sim_t *s, int op, const double *in, double *o
                                double *s1)
 {
     if (!s || !in || !out || !s0 || !s1) return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: null argument");
-    const size_t nf = (size_t)(s->d.mx + 2) * (s->d.my + 2) * (s->d.mz + 2);
+    const size_t nf = full_count(s) / (s->kind == ADS_ELASTIC ? 3 : 1);
     if (count != nf) return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: count must be n0*n1*n2");
     if (op == ADS_OP_SPLIT_SOLVE && s->kind != ADS_SCALAR_WAVE)
         return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: split solve is defined for the scalar wave");

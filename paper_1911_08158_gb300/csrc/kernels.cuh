@@ -17,6 +17,7 @@ constexpr int kBatch = 32;   // simulations per grouped launch
 // elements (sx >= mx, padding kept at zero), plane pitch sx*my.
 struct Dims {
     int mx, my, mz, sx;
+    int off;   // boundary functions dropped per side: 1 Dirichlet, 0 natural (full = unknowns)
     __host__ __device__ long long plane() const { return (long long)sx * my; }
     __host__ __device__ long long count() const { return plane() * mz; }
 };
@@ -157,7 +158,7 @@ cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, in
 // Sum of Kronecker products in one pass:
 //   out = beta*out + sum_t alpha_t (Ax_t (x) Ay_t (x) Az_t) in_t
 // (plain terms: alpha_t in_t, no contraction); row padding written as zero.
-constexpr int kMaxKronTerms = 6;
+constexpr int kMaxKronTerms = 8;
 template <typename T>
 struct KronTerm {
     const T *bx, *by, *bz;   // bands [m_pad][2p+1] per axis

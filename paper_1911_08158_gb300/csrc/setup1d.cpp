@@ -79,11 +79,12 @@ void local_basis(const std::vector<double> &t, int s, int p, double x, double *N
 
 }  // namespace
 
-Axis1D build_axis(int ne, int p, double L)
+Axis1D build_axis(int ne, int p, double L, bool natural)
 {
     if (ne < 1 || p < 1 || p > 4) throw std::invalid_argument("build_axis: ne >= 1, 1 <= p <= 4");
     Axis1D ax;
-    ax.ne = ne; ax.p = p; ax.n = ne + p; ax.m = ne + p - 2; ax.L = L;
+    ax.off = natural ? 0 : 1;
+    ax.ne = ne; ax.p = p; ax.n = ne + p; ax.m = ne + p - 2 * ax.off; ax.L = L;
     if (ax.m < 1) throw std::invalid_argument("build_axis: no interior function");
     std::vector<double> t(ne + 2 * p + 1);
     for (int i = 0; i <= p; ++i) { t[i] = 0.0; t[ne + p + i] = L; }
@@ -97,10 +98,10 @@ Axis1D build_axis(int ne, int p, double L)
             double x = a + 0.5 * h * (1.0 + gx[g]), w = 0.5 * h * gw[g];
             local_basis(t, p + e, p, x, N, dN);
             for (int r = 0; r <= p; ++r) {
-                int i = e + r - 1;                 // interior index of function e+r
+                int i = e + r - ax.off;            // unknown index of function e+r
                 if (i < 0 || i >= ax.m) continue;
                 for (int c = 0; c <= p; ++c) {
-                    int j = e + c - 1;
+                    int j = e + c - ax.off;
                     if (j < 0 || j >= ax.m) continue;
                     ax.M.at(i, j - i) += w * N[r] * N[c];
                     ax.K.at(i, j - i) += w * dN[r] * dN[c];
@@ -116,6 +117,13 @@ Axis1D build_axis(int ne, int p, double L)
     ax.lo = std::max(rm.first, std::max(rk.first, rb.first));
     ax.hi = std::min(rm.second, std::min(rk.second, rb.second));
     if (ax.hi < ax.lo) ax.hi = ax.lo;
+    // B^T in band storage: Bt[i][i+k] = B[i+k][i]
+    ax.Bt.m = ax.m;
+    ax.Bt.p = p;
+    ax.Bt.v.assign((size_t)ax.m * (2 * p + 1), 0.0);
+    for (int i = 0; i < ax.m; ++i)
+        for (int k = -p; k <= p; ++k)
+            if (i + k >= 0 && i + k < ax.m) ax.Bt.at(i, k) = ax.B.at(i + k, -k);
     return ax;
 }
 
@@ -164,7 +172,7 @@ std::vector<double> gaussian_load(const Axis1D &ax, double c, double den)
             local_basis(t, p + e, p, x, N, dN);
             double gv = w * std::exp(-(x - c) * (x - c) / den);
             for (int r = 0; r <= p; ++r) {
-                int i = e + r - 1;
+                int i = e + r - ax.off;
                 if (i >= 0 && i < ax.m) out[i] += gv * N[r];
             }
         }

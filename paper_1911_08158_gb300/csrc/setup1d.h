@@ -15,11 +15,13 @@ struct Band {
     double at(int i, int k) const { return v[(size_t)i * (2 * p + 1) + (k + p)]; }
 };
 
-// 1D interior (Dirichlet-restricted) operators of one axis.
+// 1D operators of one axis on its unknowns: the interior functions
+// (Dirichlet restriction, off = 1) or all of them (natural boundary, off = 0).
 struct Axis1D {
-    int ne = 0, p = 0, n = 0, m = 0;
+    int ne = 0, p = 0, n = 0, m = 0, off = 1;
     double L = 1.0;
     Band M, K, B;            // (N_a,N_c), (N'_a,N'_c), (N'_a,N_c)
+    Band Bt;                 // B^T (= -B up to rounding with the Dirichlet restriction)
     int lo = 0, hi = 0;      // rows [lo, hi) of M, K and B are the Toeplitz interior row
 };
 
@@ -60,7 +62,7 @@ Partition partition_fixed(const Factor &f, int seg);
 std::pair<int, int> canonicalize_interior(Band &b);
 
 void gauss_legendre(int q, double *x, double *w);
-Axis1D build_axis(int ne, int p, double L);
+Axis1D build_axis(int ne, int p, double L, bool natural = false);
 // A = M + d K, factored
 Factor factor_axis(const Axis1D &ax, double d);
 // interior load (exp(-(x-c)^2/den), N_i) with the (p+1)-point rule

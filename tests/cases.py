@@ -5,9 +5,9 @@ import numpy as np
 import oracle as ora
 
 
-def oracle_wave(case, steps, checkpoints=()):
-    """Returns {step: (u, v, a)} (full arrays, zero boundary) at the requested steps."""
-    s = ora.Space(case.n_elem, case.p)
+def oracle_wave(case, steps, checkpoints=(), boundary="dirichlet"):
+    """Returns {step: (u, v, a)} (full arrays) at the requested steps."""
+    s = ora.Space(case.n_elem, case.p, natural=boundary == "natural")
     G, rick = None, (8.0, 0.125)
     if case.source:
         src = case.source
@@ -81,9 +81,9 @@ def check_state(got, ref, precision, tau, base, what=""):
     assert_parity(got[2], ref[2], ta, what + " a (tol %.1e)" % ta)
 
 
-def oracle_elastic(case, steps, checkpoints=(), source=None):
+def oracle_elastic(case, steps, checkpoints=(), source=None, boundary="dirichlet"):
     """Returns {step: (U, V)} with V = (U^n - U^{n-1})/tau (full arrays)."""
-    s = ora.Space(case.n_elem, case.p)
+    s = ora.Space(case.n_elem, case.p, natural=boundary == "natural")
     V0 = np.zeros((3,) + s.shape)
     if case.v0:
         g = s.project_gauss(case.v0["amp"], case.v0["center"], case.v0["den"])
@@ -102,10 +102,10 @@ def oracle_elastic(case, steps, checkpoints=(), source=None):
     return out
 
 
-def gpu_elastic(case, steps, precision="fp64", checkpoints=(), source=None):
+def gpu_elastic(case, steps, precision="fp64", checkpoints=(), source=None, boundary="dirichlet"):
     from paper_1911_08158_gb300 import Simulation
     sim = Simulation(case.n_elem, case.p, case.tau, kind="elastic", lam=case.lam, mu=case.mu, rho=case.rho,
-                     precision=precision)
+                     precision=precision, boundary=boundary)
     if source:
         sim.set_source(source)
     sim.set_gaussian_state(None, case.v0)
