@@ -150,6 +150,17 @@ int ads_dims(const ads_sim_t *sim, int *n, int *comps);
  * at level n (eq. gen). */
 int ads_set_source(ads_sim_t *sim, const ads_source_t *src);
 
+/* Source with a general spatial profile: F(t) = r(t) g, with g[i] = (f, N_i)
+ * the load vector of an arbitrary (non-separable) f, integrated by the caller
+ * and given as a full coefficient array (count = n0*n1*n2; boundary entries
+ * are ignored with the Dirichlet restriction), r the Ricker wavelet of
+ * (freq, t0).  Elasticity: the body force of component c is r(t) dir[c] g
+ * (dir may be NULL = no force).  K1 adds r(t_{n+1}) g while it forms the
+ * right-hand side (one extra read of g per unknown).  mem: ADS_HOST or
+ * ADS_DEVICE.  Replaces any source set before.  Waits. */
+int ads_set_source_field(ads_sim_t *sim, const double *g, size_t count, int mem, const double *dir, double freq,
+                         double t0);
+
 /* Set the state from L2 projections (Appendix: isogeometric L2 projection,
  * exact Kronecker mass solve) of Gaussian initial displacement u0 and
  * velocity v0 (either may be NULL = zero); resets the step counter to 0.

@@ -81,6 +81,7 @@ def library() -> ctypes.CDLL:
         L.ads_destroy.restype = None
         L.ads_dims.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.ads_set_source.argtypes = [vp, ctypes.POINTER(Source)]
+        L.ads_set_source_field.argtypes = [vp, vp, sz, i, _D, d, d]
         L.ads_set_gaussian_state.argtypes = [vp, ctypes.POINTER(Gaussian), ctypes.POINTER(Gaussian)]
         L.ads_set_state.argtypes = [vp, vp, vp, vp, sz, i]
         L.ads_get_state.argtypes = [vp, vp, vp, vp, sz, i]
@@ -246,6 +247,15 @@ class Simulation:
             return
         s = Source(_gauss(src), float(src.get("freq", freq)), float(src.get("t0", t0)))
         _check(library().ads_set_source(self._h, ctypes.byref(s)))
+
+    def set_source_field(self, g, freq: float = 8.0, t0: float = 0.125, direction=None):
+        """Source r(t) g with a general load vector g (full array, one component)."""
+        count = int(np.prod(self.n))
+        ptr, mem, keep = _ptr(g, count)
+        dirp = (ctypes.c_double * 3)(*direction) if direction is not None else None
+        _check(library().ads_set_source_field(self._h, ptr, count, mem,
+                                              ctypes.cast(dirp, _D) if dirp is not None else None,
+                                              float(freq), float(t0)))
 
     def set_gaussian_state(self, u0=None, v0=None):
         g0, g1 = _gauss(u0), _gauss(v0)

@@ -65,6 +65,7 @@ struct TableSet {
     int img_bytes[NIMG] = {};
     void *gband[3] = {};                       // bands of M + eta c2 K (energies)
     void *src[3] = {};                         // separable source load vectors
+    void *srcfield = nullptr;                  // general source load vector (interior layout)
 };
 
 struct ads_sim {
@@ -394,9 +395,13 @@ ads::RhsArgs<T> rhs_args(const ads_sim *s, const T *in, T *out, int set, int tof
     a.img_bytes = ts.img_bytes[set];
     a.c2 = (T)s->c2;
     if (with_src && s->has_src) {
-        a.src.fx = (const T *)ts.src[0];
-        a.src.fy = (const T *)ts.src[1];
-        a.src.fz = (const T *)ts.src[2];
+        if (ts.srcfield) {
+            a.srcfield = (const T *)ts.srcfield;
+        } else {
+            a.src.fx = (const T *)ts.src[0];
+            a.src.fy = (const T *)ts.src[1];
+            a.src.fz = (const T *)ts.src[2];
+        }
         a.src.amp = 1.0;   // amplitude folded into the load vectors
         a.src.freq = s->src.freq;
         a.src.t0 = s->src.t0;
@@ -834,9 +839,13 @@ int add_body_force(ads_sim *s, T *r, double scale, int toff)
     for (int i = 0; i < 3; ++i) {
         const double di = s->src.shape.dir[i];
         if (di == 0.0) continue;
-        ADS_CK(ads::launch_add_source<T>(r + i * cnt, s->d, (const T *)ts.src[0], (const T *)ts.src[1],
-                                         (const T *)ts.src[2], scale * di, s->src.freq, s->src.t0, s->d_step, toff,
-                                         s->tau, s->stream));
+        if (ts.srcfield)
+            ADS_CK(ads::launch_add_field<T>(r + i * cnt, (const T *)ts.srcfield, cnt, scale * di, s->src.freq,
+                                            s->src.t0, s->d_step, toff, s->tau, s->stream));
+        else
+            ADS_CK(ads::launch_add_source<T>(r + i * cnt, s->d, (const T *)ts.src[0], (const T *)ts.src[1],
+                                             (const T *)ts.src[2], scale * di, s->src.freq, s->src.t0, s->d_step,
+                                             toff, s->tau, s->stream));
     }
     return ADS_OK;
 }
@@ -1492,11 +1501,14 @@ int ads_set_source(ads_sim_t *s, const ads_source_t *src)
     if (!s) return fail(ADS_ERR_INVALID_ARG, "ads_set_source: null sim");
     cudaSetDevice(s->device);
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(ADS_ERR_CUDA, "ads_set_source: stream error");
-    for (TableSet *ts : {&s->t64, &s->t32})
+    for (TableSet *ts : {&s->t64, &s->t32}) {
         for (int a = 0; a < 3; ++a) {
             dfree(s, ts->src[a]);
             ts->src[a] = nullptr;
         }
+        dfree(s, ts->srcfield);
+        ts->srcfield = nullptr;
+    }
     s->has_src = false;
     for (int a = 0; a < 3; ++a) s->hsrc[a].clear();
     if (!src) return rebuild_images(s);
@@ -1512,6 +1524,39 @@ int ads_set_source(ads_sim_t *s, const ads_source_t *src)
         if (rc) return rc;
         if (s->prec == ADS_FP32 && (rc = upload<float>(s, g, &s->t32.src[a]))) return rc;
     }
+    s->has_src = true;
+    return rebuild_images(s);
+}
+
+int ads_set_source_field(ads_sim_t *s, const double *g, size_t count, int mem, const double *dir, double freq,
+                         double t0)
+{
+    if (!s || !g) return fail(ADS_ERR_INVALID_ARG, "ads_set_source_field: null argument");
+    if (mem != ADS_HOST && mem != ADS_DEVICE) return fail(ADS_ERR_INVALID_ARG, "ads_set_source_field: mem");
+    const size_t nf = full_count(s) / (s->kind == ADS_ELASTIC ? 3 : 1);
+    if (count != nf) return fail(ADS_ERR_INVALID_ARG, "ads_set_source_field: count must be n0*n1*n2");
+    if (!std::isfinite(freq) || !std::isfinite(t0)) return fail(ADS_ERR_INVALID_ARG, "ads_set_source_field: freq, t0");
+    int rc = ads_set_source(s, nullptr);   // drop any previous source
+    if (rc) return rc;
+    Scratch sc(s);
+    const size_t ni = (size_t)s->d.count() * sizeof(double);
+    void *f64 = dalloc(s, ni);
+    if (!f64) return fail(ADS_ERR_OOM, "ads_set_source_field: device allocation failed");
+    s->t64.srcfield = f64;
+    if ((rc = stage_in(s, sc, g, mem, count, (double *)f64, 1.0))) return rc;
+    if (s->prec == ADS_FP32) {
+        void *f32 = dalloc(s, (size_t)s->d.count() * sizeof(float));
+        if (!f32) return fail(ADS_ERR_OOM, "ads_set_source_field: device allocation failed");
+        s->t32.srcfield = f32;
+        ADS_CK(ads::launch_convert_from<float>((const double *)f64, (float *)f32, s->d.count(), s->stream));
+    }
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    std::memset(&s->src, 0, sizeof(s->src));
+    s->src.shape.amp = 1.0;
+    if (dir)
+        for (int i = 0; i < 3; ++i) s->src.shape.dir[i] = dir[i];
+    s->src.freq = freq;
+    s->src.t0 = t0;
     s->has_src = true;
     return rebuild_images(s);
 }

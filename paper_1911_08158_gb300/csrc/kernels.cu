@@ -462,6 +462,18 @@ __global__ void k_add_source(T *out, Dims d, const T *fx, const T *fy, const T *
 }
 
 template <typename T>
+__global__ void k_add_field(T *out, const T *field, long long n, double scale, double freq, double t0,
+                            const long long *step, int toff, double tau)
+{
+    __shared__ T s_c;
+    if (threadIdx.x == 0) s_c = (T)(scale * ricker_dev(freq, t0, (double)(step[0] + toff) * tau));
+    __syncthreads();
+    const T c = s_c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] += c * field[i];
+}
+
+template <typename T>
 __global__ void k_el_to_uv(const T *U, const T *Up, double *u, double *v, long long n, double tau)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -800,6 +812,15 @@ cudaError_t launch_add_source(T *out, Dims d, const T *fx, const T *fy, const T 
 }
 
 template <typename T>
+cudaError_t launch_add_field(T *out, const T *field, long long n, double scale, double freq, double t0,
+                             const long long *step, int toff, double tau, cudaStream_t s)
+{
+    ++g_launches;
+    k_add_field<T><<<grid_for(n, 256), 256, 0, s>>>(out, field, n, scale, freq, t0, step, toff, tau);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long long n, double tau, cudaStream_t s)
 {
     ++g_launches;
@@ -828,6 +849,8 @@ cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long 
     template cudaError_t launch_add_converted<T>(const T *, double *, long long, cudaStream_t);                     \
     template cudaError_t launch_add_source<T>(T *, Dims, const T *, const T *, const T *, double, double, double,   \
                                               const long long *, int, double, cudaStream_t);                       \
+    template cudaError_t launch_add_field<T>(T *, const T *, long long, double, double, double, const long long *, \
+                                             int, double, cudaStream_t);                                           \
     template cudaError_t launch_el_to_uv<T>(const T *, const T *, double *, double *, long long, double, cudaStream_t);
 
 ADS_INST(float)

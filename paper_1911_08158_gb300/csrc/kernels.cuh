@@ -75,6 +75,7 @@ struct RhsArgs {
     double tau;
     int ty;               // rows per tile (y); fused y sweep iff ty == my
     int *err;             // device error word (bounded waits)
+    const T *srcfield;    // non-null: F(t) = r(t) srcfield (general load vector, interior layout)
     int direct;           // 1: `in` is the RHS itself (no quadrature): out = Ax^{-1} [Ay^{-1}] in
     int pair;             // 1 (FP32): a 2-CTA cluster per z-plane (fused y sweep across the pair)
 };
@@ -232,6 +233,10 @@ cudaError_t launch_atm_update(T *U, T *Up, const T *d, long long n, long long *s
 template <typename T>
 cudaError_t launch_add_source(T *out, Dims d, const T *fx, const T *fy, const T *fz, double scale, double freq,
                               double t0, const long long *step, int toff, double tau, cudaStream_t s);
+// out += scale * ricker(t) * field,  t = (step[0] + toff) * tau  (general load vector)
+template <typename T>
+cudaError_t launch_add_field(T *out, const T *field, long long n, double scale, double freq, double t0,
+                             const long long *step, int toff, double tau, cudaStream_t s);
 // FP64 views of the elastic state: u = U, v = (U - Up)/tau
 template <typename T>
 cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long long n, double tau, cudaStream_t s);

@@ -348,7 +348,10 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
             acc1 += bk[q] * a1[k + q];
             acc2 += bm[q] * a2[k + q];
         }
-        v[k] = (fxb ? rowF * fxb[k] : T(0)) - c2 * (acc1 + acc2);
+        // a general load vector (global row) is read only inside the line; the
+        // separable one (shared memory) is padded with zeros
+        const bool fin = MODE == kSegMiddle || MODE == kSegFirst || x < mx;
+        v[k] = (fxb && fin ? rowF * fxb[k] : T(0)) - c2 * (acc1 + acc2);
     }
     seg_pass1<T, P, SEG>(fb, v);   // rows are independent above; the chain is here
 }
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(RhsThreads<T, PAIR>::value, RhsThreads<T, PAIR
     T *lyb = lxb + line_image_elems_dev(P, mxp, a.lx.S);
     const LineSm<T> LX = line_carve<T, P>(lxb, mxp, a.lx.S);
     const LineSm<T> LY = line_carve<T, P>(lyb, myp, a.ly.S);
-    const bool has_src = a.src.fx != nullptr;
+    const bool has_src = a.src.fx != nullptr || a.srcfield != nullptr;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(RhsThreads<T, PAIR>::value, RhsThreads<T, PAIR
             const T *row1 = S1 + (size_t)l * RS;
             const T *row2 = S2 + (size_t)l * RS;
             const int y = y0 + l;
-            const T rowF = has_src ? s_r * sfy[y] * a.src.fz[z] : T(0);
+            const T rowF = !has_src ? T(0) : (a.srcfield ? s_r : s_r * sfy[y] * a.src.fz[z]);
             const T c2 = a.c2;
             const int xlo = a.bandM[0].lo, xhi = a.bandM[0].hi;
             T mxm[W], mxk[W];
@@ -551,7 +554,8 @@ __global__ void __launch_bounds__(RhsThreads<T, PAIR>::value, RhsThreads<T, PAIR
                 mxm[k] = bMx[mid * W + k];
                 mxk[k] = bKx[mid * W + k];
             }
-            const T *srcF = has_src ? sfx : nullptr;
+            const T *srcF = !has_src ? nullptr
+                                     : (a.srcfield ? a.srcfield + (long long)z * plane + (long long)y * sx : sfx);
             const T *fb = LX.fac + b0 * W;
             // kinds: interior segments take bands from registers; the first reads its
             // head rows (< kHeadRows >= Toeplitz lo) from the table; the last reads
