@@ -149,7 +149,8 @@ class Space:
     """Tensor-product spline space on [0,L]^3: homogeneous Dirichlet
     restriction (first and last function per axis dropped), or, with
     natural=True, every basis function kept (traction-free / natural
-    boundary)."""
+    boundary).  ne[2] == 0: a 2D problem on [0,Lx] x [0,Ly] (one constant
+    function along z, arrays of shape (1, ny, nx))."""
 
     def __init__(self, ne, p: int, L=(1.0, 1.0, 1.0), natural: bool = False):
         ne = tuple(int(v) for v in (ne if np.ndim(ne) else (ne, ne, ne)))
@@ -161,7 +162,8 @@ class Space:
         m = (ctypes.c_int * 3)()
         lib().ora_space_dims(self._h, m)
         self.m = (m[0], m[1], m[2])                 # (mx, my, mz)
-        self.n = tuple(v + p for v in ne)           # full basis counts
+        self.dim2 = ne[2] == 0
+        self.n = (ne[0] + p, ne[1] + p, 1 if self.dim2 else ne[2] + p)   # full basis counts
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -298,11 +300,16 @@ class Space:
         if self.natural:
             return np.array(a, dtype=np.float64)
         out = np.zeros(a.shape[:-3] + (self.n[2], self.n[1], self.n[0]))
-        out[..., 1:-1, 1:-1, 1:-1] = a
+        if self.dim2:
+            out[..., 1:-1, 1:-1] = a
+        else:
+            out[..., 1:-1, 1:-1, 1:-1] = a
         return out
 
     def interior(self, a):
         """Full coefficient array -> the unknowns (inverse of pad)."""
         if self.natural:
             return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        if self.dim2:
+            return np.ascontiguousarray(np.asarray(a)[..., 1:-1, 1:-1])
         return np.ascontiguousarray(np.asarray(a)[..., 1:-1, 1:-1, 1:-1])

@@ -178,13 +178,26 @@ typedef struct {
 
 /* natural != 0 keeps every basis function (traction-free / natural boundary,
  * Sec. 5); otherwise the homogeneous Dirichlet restriction drops the first
- * and last function per axis. */
+ * and last function per axis.  ne[2] == 0 is a 2D problem (Sec. 2 derives
+ * the method in 2D): the z axis carries one constant function, M = [1],
+ * K = B = [0], so every 3D operator below reduces to its 2D form. */
 ora_space *ora_space_new_bc(const int *ne, int p, const double *L, int natural)
 {
     ora_space *s = (ora_space *)calloc(1, sizeof(ora_space));
     s->p = p;
     s->off = natural ? 0 : 1;
     for (int a = 0; a < 3; a++) {
+        if (a == 2 && ne[2] == 0) {
+            s->ne[2] = 0;
+            s->n[2] = s->m[2] = 1;
+            s->L[2] = 1.0;
+            s->M[2] = (double *)calloc(1, sizeof(double));
+            s->K[2] = (double *)calloc(1, sizeof(double));
+            s->B[2] = (double *)calloc(1, sizeof(double));
+            s->M[2][0] = 1.0;
+            s->t[2] = NULL;
+            continue;
+        }
         int n = ne[a] + p, m = n - 2 * s->off;
         s->ne[a] = ne[a];
         s->n[a] = n;
@@ -387,7 +400,17 @@ void ora_load_gauss(const ora_space *s, double amp, const double *c, double den,
     /* basis values at every quadrature point of every element, per axis */
     double *V[3];
     double *X[3], *W[3];
+    const int dim2 = s->ne[2] == 0;
     for (int a = 0; a < 3; a++) {
+        if (a == 2 && dim2) {   /* one "element", one point of weight 1, value 1 */
+            V[2] = (double *)calloc((size_t)q * (p + 1), sizeof(double));
+            X[2] = (double *)calloc((size_t)q, sizeof(double));
+            W[2] = (double *)calloc((size_t)q, sizeof(double));
+            V[2][0] = 1.0;
+            W[2][0] = 1.0;
+            X[2][0] = c[2];
+            continue;
+        }
         int ne = s->ne[a], n = s->n[a];
         V[a] = (double *)malloc(sizeof(double) * (size_t)ne * q * (p + 1));
         X[a] = (double *)malloc(sizeof(double) * (size_t)ne * q);
@@ -408,18 +431,19 @@ void ora_load_gauss(const ora_space *s, double amp, const double *c, double den,
         free(Nb);
         free(dNb);
     }
-    for (int ez = 0; ez < s->ne[2]; ez++)
+    const int nez = dim2 ? 1 : s->ne[2], qz = dim2 ? 1 : q, offz = dim2 ? 0 : s->off;
+    for (int ez = 0; ez < nez; ez++)
         for (int ey = 0; ey < s->ne[1]; ey++)
             for (int ex = 0; ex < s->ne[0]; ex++)
-                for (int gz = 0; gz < q; gz++)
+                for (int gz = 0; gz < qz; gz++)
                     for (int gy = 0; gy < q; gy++)
                         for (int gxi = 0; gxi < q; gxi++) {
                             int iz = ez * q + gz, iy = ey * q + gy, ix = ex * q + gxi;
                             double dx = X[0][ix] - c[0], dy = X[1][iy] - c[1], dz = X[2][iz] - c[2];
                             double g = amp * exp(-(dx * dx + dy * dy + dz * dz) / den);
                             double w = W[0][ix] * W[1][iy] * W[2][iz] * g;
-                            for (int bz = 0; bz <= p; bz++) {
-                                int k = ez + bz - s->off;     /* unknown index */
+                            for (int bz = 0; bz <= (dim2 ? 0 : p); bz++) {
+                                int k = ez + bz - offz;       /* unknown index */
                                 if (k < 0 || k >= s->m[2]) continue;
                                 double vz = V[2][iz * (p + 1) + bz];
                                 for (int by = 0; by <= p; by++) {

@@ -315,7 +315,8 @@ int build_tables(ads_sim *s, TableSet &ts)
         if ((rc = upload<T>(s, s->hM[a], &ts.M[a]))) return rc;
         if ((rc = upload<T>(s, s->hK[a], &ts.K[a]))) return rc;
         if ((rc = upload<T>(s, pad_rows(ax.B.v, ax.m, W, mp, false), &ts.B[a]))) return rc;
-        if (s->d.off == 0 && (rc = upload<T>(s, pad_rows(ax.Bt.v, ax.m, W, mp, false), &ts.Bt[a]))) return rc;
+        if ((s->d.off == 0 || ax.ne == 0) && (rc = upload<T>(s, pad_rows(ax.Bt.v, ax.m, W, mp, false), &ts.Bt[a])))
+            return rc;
         for (int set = 0; set < NSETS; ++set)
             if (!s->hline[set][a].empty() && (rc = upload_line<T>(s, set, a, &ts.line[set][a]))) return rc;
         if (s->kind == ADS_SCALAR_WAVE) {
@@ -525,8 +526,8 @@ int check_device_error(ads_sim *s)
 
 size_t full_count(const ads_sim *s)
 {
-    const int o = 2 * s->d.off;
-    return (size_t)(s->d.mx + o) * (s->d.my + o) * (s->d.mz + o) * (s->kind == ADS_ELASTIC ? 3 : 1);
+    const int o = 2 * s->d.off, oz = 2 * s->d.offz;
+    return (size_t)(s->d.mx + o) * (s->d.my + o) * (s->d.mz + oz) * (s->kind == ADS_ELASTIC ? 3 : 1);
 }
 
 // a = M^{-1}(F(t_n) - K u) for an FP64 interior u
@@ -1336,7 +1337,8 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     if (grid->boundary != ADS_DIRICHLET && grid->boundary != ADS_NATURAL)
         return fail(ADS_ERR_INVALID_ARG, "ads_create: boundary must be ADS_DIRICHLET or ADS_NATURAL");
     const int drop = grid->boundary == ADS_NATURAL ? 0 : 2;
-    for (int a = 0; a < 3; ++a) {
+    const bool plane2d = grid->n_elem[2] == 0;   // a 2D problem on [0,Lx] x [0,Ly]
+    for (int a = 0; a < (plane2d ? 2 : 3); ++a) {
         if (grid->n_elem[a] < 1) return fail(ADS_ERR_INVALID_ARG, "ads_create: n_elem must be >= 1");
         if (!(grid->length[a] > 0.0)) return fail(ADS_ERR_INVALID_ARG, "ads_create: length must be > 0");
         if (grid->n_elem[a] + p - drop < 1) return fail(ADS_ERR_INVALID_ARG, "ads_create: no interior basis function");
@@ -1387,7 +1389,9 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     }
     try {
         for (int a = 0; a < 3; ++a)
-            s->ax[a] = ads::build_axis(grid->n_elem[a], p, grid->length[a], grid->boundary == ADS_NATURAL);
+            s->ax[a] = (a == 2 && plane2d) ? ads::trivial_axis(p)
+                                           : ads::build_axis(grid->n_elem[a], p, grid->length[a],
+                                                             grid->boundary == ADS_NATURAL);
     } catch (const std::exception &e) {
         ads_destroy(s);
         return fail(ADS_ERR_INVALID_ARG, e.what());
@@ -1397,6 +1401,7 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     s->d.mz = s->ax[2].m;
     s->d.sx = (s->d.mx + 7) / 8 * 8;
     s->d.off = grid->boundary == ADS_NATURAL ? 0 : 1;
+    s->d.offz = plane2d ? 0 : s->d.off;
     {
         const int m3[3] = {s->d.mx, s->d.my, s->d.mz};
         s->seg = ads::choose_seg(m3);   // 33-row segments when they save segments (m = 32 s + 1)
@@ -1490,7 +1495,7 @@ int ads_dims(const ads_sim_t *s, int *n, int *comps)
     if (n) {
         n[0] = s->d.mx + 2 * s->d.off;
         n[1] = s->d.my + 2 * s->d.off;
-        n[2] = s->d.mz + 2 * s->d.off;
+        n[2] = s->d.mz + 2 * s->d.offz;
     }
     if (comps) *comps = s->kind == ADS_ELASTIC ? 3 : 1;
     return ADS_OK;
@@ -1915,8 +1920,9 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
     size_t m[3], mp[3], S[3];
     int mi[3];
     for (int a = 0; a < 3; ++a) {
-        const long long me = (long long)grid->n_elem[a] + p - (grid->boundary == ADS_NATURAL ? 0 : 2);
-        if (grid->n_elem[a] < 1 || me < 1 || me > (1 << 20)) return 0;
+        long long me = (long long)grid->n_elem[a] + p - (grid->boundary == ADS_NATURAL ? 0 : 2);
+        if (a == 2 && grid->n_elem[2] == 0) me = 1;   // 2D
+        else if (grid->n_elem[a] < 1 || me < 1 || me > (1 << 20)) return 0;
         m[a] = (size_t)me;
         mi[a] = (int)me;
     }

@@ -242,7 +242,7 @@ __global__ void k_pack(const double *__restrict__ full, T *__restrict__ in, Dims
 {
     const long long n = d.count();
     const long long plane = d.plane();
-    const int o = d.off;
+    const int o = d.off, oz = d.offz;
     const int nx = d.mx + 2 * o, ny = d.my + 2 * o;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -251,7 +251,7 @@ __global__ void k_pack(const double *__restrict__ full, T *__restrict__ in, Dims
         const int y = (int)(rem / d.sx);
         const int x = (int)(rem - (long long)y * d.sx);
         T v = T(0);
-        if (x < d.mx) v = (T)(scale * full[((long long)(z + o) * ny + (y + o)) * nx + (x + o)]);
+        if (x < d.mx) v = (T)(scale * full[((long long)(z + oz) * ny + (y + o)) * nx + (x + o)]);
         in[idx] = v;
     }
 }
@@ -259,8 +259,8 @@ __global__ void k_pack(const double *__restrict__ full, T *__restrict__ in, Dims
 template <typename T>
 __global__ void k_unpack(const T *__restrict__ in, double *__restrict__ full, Dims d)
 {
-    const int o = d.off;
-    const int nx = d.mx + 2 * o, ny = d.my + 2 * o, nz = d.mz + 2 * o;
+    const int o = d.off, oz = d.offz;
+    const int nx = d.mx + 2 * o, ny = d.my + 2 * o, nz = d.mz + 2 * oz;
     const long long n = (long long)nx * ny * nz;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -269,8 +269,8 @@ __global__ void k_unpack(const T *__restrict__ in, double *__restrict__ full, Di
         const int y = (int)(rem / nx);
         const int x = (int)(rem - (long long)y * nx);
         double v = 0.0;
-        if (x >= o && x < d.mx + o && y >= o && y < d.my + o && z >= o && z < d.mz + o)
-            v = (double)in[(long long)(z - o) * d.plane() + (long long)(y - o) * d.sx + (x - o)];
+        if (x >= o && x < d.mx + o && y >= o && y < d.my + o && z >= oz && z < d.mz + oz)
+            v = (double)in[(long long)(z - oz) * d.plane() + (long long)(y - o) * d.sx + (x - o)];
         full[idx] = v;
     }
 }
@@ -694,7 +694,7 @@ template <typename T>
 cudaError_t launch_unpack(const T *in, double *full, Dims d, cudaStream_t s)
 {
     ++g_launches;
-    long long n = (long long)(d.mx + 2 * d.off) * (d.my + 2 * d.off) * (d.mz + 2 * d.off);
+    long long n = (long long)(d.mx + 2 * d.off) * (d.my + 2 * d.off) * (d.mz + 2 * d.offz);
     k_unpack<T><<<grid_for(n, 256), 256, 0, s>>>(in, full, d);
     return cudaGetLastError();
 }

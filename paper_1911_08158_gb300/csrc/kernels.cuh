@@ -18,6 +18,7 @@ constexpr int kBatch = 32;   // simulations per grouped launch
 struct Dims {
     int mx, my, mz, sx;
     int off;   // boundary functions dropped per side: 1 Dirichlet, 0 natural (full = unknowns)
+    int offz;  // the same along z (0 for a 2D problem: one constant function along z)
     __host__ __device__ long long plane() const { return (long long)sx * my; }
     __host__ __device__ long long count() const { return plane() * mz; }
 };

@@ -127,6 +127,16 @@ Axis1D build_axis(int ne, int p, double L, bool natural)
     return ax;
 }
 
+Axis1D trivial_axis(int p)
+{
+    Axis1D ax;
+    ax.ne = 0; ax.p = p; ax.n = 1; ax.m = 1; ax.off = 0; ax.L = 1.0;
+    for (Band *b : {&ax.M, &ax.K, &ax.B, &ax.Bt}) { b->m = 1; b->p = p; b->v.assign((size_t)(2 * p + 1), 0.0); }
+    ax.M.at(0, 0) = 1.0;
+    ax.lo = ax.hi = 0;
+    return ax;
+}
+
 Factor factor_axis(const Axis1D &ax, double d)
 {
     const int m = ax.m, p = ax.p, W = 2 * p + 1;
@@ -158,6 +168,7 @@ Factor factor_axis(const Axis1D &ax, double d)
 
 std::vector<double> gaussian_load(const Axis1D &ax, double c, double den)
 {
+    if (ax.ne == 0) return std::vector<double>(1, 1.0);   // the missing axis of a 2D problem
     const int p = ax.p, ne = ax.ne;
     std::vector<double> t(ne + 2 * p + 1);
     for (int i = 0; i <= p; ++i) { t[i] = 0.0; t[ne + p + i] = ax.L; }

@@ -63,6 +63,9 @@ std::pair<int, int> canonicalize_interior(Band &b);
 
 void gauss_legendre(int q, double *x, double *w);
 Axis1D build_axis(int ne, int p, double L, bool natural = false);
+// The axis of a 2D problem's missing dimension: one constant function, M = [1],
+// K = B = [0] (band width of degree p), so 3D operators act as their 2D ones.
+Axis1D trivial_axis(int p);
 // A = M + d K, factored
 Factor factor_axis(const Axis1D &ax, double d);
 // interior load (exp(-(x-c)^2/den), N_i) with the (p+1)-point rule

@@ -119,3 +119,38 @@ def elastic_dense(ne, p, lam, mu, L=(1.0, 1.0, 1.0), natural=False):
                                         blk = blk + mu * gg
                                     S[np.ix_(a * N + I, b * N + I)] += w * blk
     return S
+
+
+def elastic_dense_2d(ne, p, lam, mu, L=(1.0, 1.0)):
+    """Dense plane-strain elasticity stiffness (components x, y) on the
+    interior DOFs of a 2D spline space, by direct 2D quadrature of
+    2 mu e(w):e(u) + lam div w div u.  Component-major, x fastest."""
+    T = [tables(ne[a], p, L[a]) for a in range(2)]
+    m = [ne[a] + p - 2 for a in range(2)]
+    N = m[0] * m[1]
+    S = np.zeros((2 * N, 2 * N))
+    q = p + 1
+    for ey in range(ne[1]):
+        for ex in range(ne[0]):
+            idx = []
+            for by in range(q):
+                for bx in range(q):
+                    i, j = ex + bx - 1, ey + by - 1
+                    idx.append(j * m[0] + i if 0 <= i < m[0] and 0 <= j < m[1] else -1)
+            idx = np.array(idx)
+            keep = idx >= 0
+            I = idx[keep]
+            for gy in range(q):
+                for gx in range(q):
+                    w = T[0][2][ex, gx] * T[1][2][ey, gy]
+                    vx, dx = T[0][0][ex, gx], T[0][1][ex, gx]
+                    vy, dy = T[1][0][ey, gy], T[1][1][ey, gy]
+                    G = np.stack([np.outer(vy, dx).ravel(), np.outer(dy, vx).ravel()])[:, keep]   # grad of each function
+                    gg = G.T @ G
+                    for a in range(2):
+                        for b in range(2):
+                            blk = mu * np.outer(G[b], G[a]) + lam * np.outer(G[a], G[b])
+                            if a == b:
+                                blk = blk + mu * gg
+                            S[np.ix_(a * N + I, b * N + I)] += w * blk
+    return S
