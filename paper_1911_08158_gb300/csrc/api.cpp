@@ -636,8 +636,10 @@ int pwave_refine_step(ads_sim *s, bool write_a, KernelTimer *kt)
     ADS_CK(ads::launch_axpby(-1.0, T, 1.0, R, n, s->stream));
     if (kt && (rc = kt->mark(s->stream, "correction_sweeps"))) return rc;
     ADS_CK(ads::launch_convert_from<float>(R, X, n, s->stream));
-    ADS_CK(ads::launch_solve_x<float>(s->p, (const float *)s->t32.line[SET_SPLIT][0].base, X, s->d, s->stream));
-    if ((rc = sweeps_yz<float>(s, X, SET_SPLIT, false))) return rc;
+    ads::RhsArgs<float> rd = rhs_args<float>(s, X, X, SET_SPLIT, 0, false);   // given RHS: x (and y) sweeps
+    rd.direct = 1;
+    ADS_CK(ads::launch_rhs_group<float>(s->p, &rd, 1, s->stream));
+    if ((rc = sweeps_yz<float>(s, X, SET_SPLIT, rd.ty == s->d.my || rd.pair))) return rc;
     ADS_CK(ads::launch_add_converted<float>(X, A64, n, s->stream));
     ADS_CK(ads::launch_convert_from<float>(A64, X, n, s->stream));
     if (kt && (rc = kt->mark(s->stream, "update"))) return rc;
@@ -698,21 +700,6 @@ int pwave_group_step(const std::vector<ads_sim *> &g, cudaStream_t st, bool writ
 //   Ups_ii = mu (Kx My Mz + Mx Ky Mz + Mx My Kz) + (mu + lam) [K on axis i]
 //   Ups_ij = -(mu + lam) [B on axis i, B on axis j, M on the third],  i != j
 // (bilinear form 2 mu e(w):e(u) + lam div w div u, Sec. 5).
-
-// out = (beta ? out : 0) + coef (A0 (x) A1 (x) A2) in; which[a]: 0 = M, 1 = K, 2 = B
-template <typename T>
-int kron3(ads_sim *s, const T *in, T *out, const int *which, T coef, bool accumulate, T *ta, T *tb)
-{
-    const TableSet &ts = tables_for<T>(s);
-    const void *band[3];
-    for (int a = 0; a < 3; ++a)
-        band[a] = which[a] == 0 ? ts.M[a] : (which[a] == 1 ? ts.K[a] : (which[a] == 2 ? ts.B[a] : ts.Bt[a]));
-    (void)ta;
-    (void)tb;
-    ADS_CK(ads::launch_kron3<T>(s->p, (const T *)band[0], (const T *)band[1], (const T *)band[2], in, out, s->d, coef,
-                                accumulate ? T(1) : T(0), s->stream));
-    return ADS_OK;
-}
 
 // Kronecker term coef * (A0 (x) A1 (x) A2) in; which[a]: 0 = M, 1 = K, 2 = B
 template <typename T>

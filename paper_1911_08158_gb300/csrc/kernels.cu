@@ -55,72 +55,6 @@ __global__ void k_axis_apply(const T *__restrict__ band, int axis, const T *__re
     }
 }
 
-// One-pass Kronecker product  out = beta*out + alpha*(Ax (x) Ay (x) Az) in,
-// one CTA per (z-plane, tile of ty rows): z-contraction of rows y0-P ..
-// y0+ty+P-1 into shared memory, y-contraction into a second buffer, then
-// x-contraction and the store (row padding written as zero).
-template <typename T, int P>
-__global__ void __launch_bounds__(256) k_kron3(const T *__restrict__ bx, const T *__restrict__ by,
-                                               const T *__restrict__ bz, const T *__restrict__ in, T *out, Dims d,
-                                               T alpha, T beta, int ty)
-{
-    constexpr int W = 2 * P + 1;
-    extern __shared__ __align__(16) unsigned char kron_smem[];
-    const int sx = d.sx, mx = d.mx, my = d.my, mz = d.mz;
-    T *Tz = reinterpret_cast<T *>(kron_smem);   // [(ty + 2P)][sx]
-    T *Uy = Tz + (size_t)(ty + 2 * P) * sx;     // [ty][sx]
-    const int z = blockIdx.y, y0 = blockIdx.x * ty;
-    const int tye = min(ty, my - y0);
-    const long long plane = d.plane();
-    T cz[W];
-    bool zok[W];
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-        cz[k] = bz[z * W + k];
-        zok[k] = z + k - P >= 0 && z + k - P < mz;
-    }
-    const int nr = tye + 2 * P;
-    for (int idx = threadIdx.x; idx < nr * mx; idx += blockDim.x) {
-        const int r = idx / mx, x = idx - r * mx;
-        const int y = y0 - P + r;
-        T acc = T(0);
-        if (y >= 0 && y < my) {
-            const T *src = in + (long long)(z - P) * plane + (long long)y * sx + x;
-#pragma unroll
-            for (int k = 0; k < W; ++k)
-                if (zok[k]) acc += cz[k] * src[(long long)k * plane];
-        }
-        Tz[(size_t)r * sx + x] = acc;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < tye * mx; idx += blockDim.x) {
-        const int l = idx / mx, x = idx - l * mx;
-        const T *row = by + (size_t)(y0 + l) * W;
-        T acc = T(0);
-#pragma unroll
-        for (int q = 0; q < W; ++q) acc += row[q] * Tz[(size_t)(l + q) * sx + x];
-        Uy[(size_t)l * sx + x] = acc;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < tye * sx; idx += blockDim.x) {
-        const int l = idx / sx, x = idx - l * sx;
-        T *o = out + (long long)z * plane + (long long)(y0 + l) * sx + x;
-        if (x >= mx) {
-            *o = T(0);
-            continue;
-        }
-        const T *row = bx + (size_t)x * W;
-        const T *u = Uy + (size_t)l * sx;
-        T acc = T(0);
-#pragma unroll
-        for (int r = 0; r < W; ++r) {
-            const int xx = x + r - P;
-            if (xx >= 0 && xx < mx) acc += row[r] * u[xx];
-        }
-        *o = (beta == T(0) ? T(0) : beta * *o) + alpha * acc;
-    }
-}
-
 // Sum of Kronecker products, one CTA per (z-plane, tile of ty rows): the
 // terms are applied one after another through two staging buffers
 // (z-contraction, y-contraction) and accumulated into a third, which is
@@ -638,39 +572,6 @@ cudaError_t launch_kron_sum(int p, const KronSum<T> &ks, T *out, Dims d, cudaStr
 #undef C
 }
 
-template <typename T, int P>
-cudaError_t kron3_impl(dim3 grid, size_t smem, cudaStream_t s, const T *bx, const T *by, const T *bz, const T *in,
-                       T *out, Dims d, T alpha, T beta, int ty)
-{
-    static size_t smem_set = 48 * 1024;   // per instantiation: opt-in dynamic shared memory (set outside capture)
-    if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_kron3<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-    }
-    k_kron3<T, P><<<grid, 256, smem, s>>>(bx, by, bz, in, out, d, alpha, beta, ty);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_kron3(int p, const T *bx, const T *by, const T *bz, const T *in, T *out, Dims d, T alpha, T beta,
-                         cudaStream_t s)
-{
-    // rows per tile: both buffers within 96 KB of shared memory
-    const size_t row = (size_t)d.sx * sizeof(T);
-    int ty = (int)((96 * 1024 / row - 2 * p) / 2);
-    if (ty > 16) ty = 16;
-    if (ty < 1) ty = 1;
-    if (ty > d.my) ty = d.my;
-    const size_t smem = (size_t)(2 * ty + 2 * p) * row;
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    dim3 grid((d.my + ty - 1) / ty, d.mz);
-    ++g_launches;
-#define C(P) kron3_impl<T, P>(grid, smem, s, bx, by, bz, in, out, d, alpha, beta, ty)
-    ADS_DISPATCH_P(p, C)
-#undef C
-}
-
 template <typename T>
 cudaError_t launch_solve_x(int p, const T *fac, T *data, Dims d, cudaStream_t s)
 {
@@ -833,7 +734,6 @@ cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long 
     template cudaError_t launch_col<T>(int, int, const ColArgs<T> &, cudaStream_t);                                \
     template cudaError_t launch_axis_apply<T>(int, const T *, int, const T *, T *, Dims, T, T, int, cudaStream_t); \
     template cudaError_t launch_solve_x<T>(int, const T *, T *, Dims, cudaStream_t);                               \
-    template cudaError_t launch_kron3<T>(int, const T *, const T *, const T *, const T *, T *, Dims, T, T, cudaStream_t); \
     template cudaError_t launch_kron_sum<T>(int, const KronSum<T> &, T *, Dims, cudaStream_t);                     \
     template cudaError_t launch_pack<T>(const double *, T *, Dims, double, cudaStream_t);                          \
     template cudaError_t launch_unpack<T>(const T *, double *, Dims, cudaStream_t);                                \

@@ -176,11 +176,6 @@ struct KronSum {
 };
 template <typename T>
 cudaError_t launch_kron_sum(int p, const KronSum<T> &ks, T *out, Dims d, cudaStream_t s);
-// out = beta*out + alpha*(Ax (x) Ay (x) Az) in in one pass (bands [m_pad][2p+1]
-// of each axis); row padding of out is written as zero
-template <typename T>
-cudaError_t launch_kron3(int p, const T *bx, const T *by, const T *bz, const T *in, T *out, Dims d, T alpha, T beta,
-                         cudaStream_t s);
 // out = band applied along axis (0,1,2) to in; out = beta*out + alpha*(A in)
 template <typename T>
 cudaError_t launch_axis_apply(int p, const T *band, int axis, const T *in, T *out, Dims d, T alpha, T beta,
