@@ -34,8 +34,10 @@ int fail(int code, const std::string &msg)
 #define ADS_CK(expr)                                                                              \
     do {                                                                                          \
         cudaError_t e_ = (expr);                                                                  \
-        if (e_ != cudaSuccess)                                                                    \
+        if (e_ != cudaSuccess) {                                                                  \
+            cudaGetLastError(); /* a failed launch or attribute call leaves no pending error */    \
             return fail(ADS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));        \
+        }                                                                                         \
     } while (0)
 
 }  // namespace
@@ -519,6 +521,7 @@ int check_device_error(ads_sim *s)
     if (e != 0) {
         cudaMemset(s->d_err, 0, sizeof(int));
         if (e == 2) return fail(ADS_ERR_CUDA, "a kernel found a misaligned TMA shared-memory address and skipped it");
+        if (e == 3) return fail(ADS_ERR_UNSUPPORTED, "a sweep kernel was launched with fewer warps than line segments");
         return fail(ADS_ERR_TIMEOUT, "a device-side wait timed out (TMA transfer did not complete)");
     }
     return ADS_OK;
@@ -1136,7 +1139,7 @@ std::vector<std::pair<int, int>> tile_candidates(const ads_sim *s)
     const int Sx = segs(s, s->d.mx), Sy = segs(s, s->d.my), my = s->d.my;
     std::vector<std::pair<int, int>> c;
     if (ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg) <= 220 * 1024) c.push_back({my, 0});
-    if (el == 4 && my >= 2 && ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg, 1) <= 110 * 1024)
+    if (el == 4 && my >= 2 && Sx <= 8 && Sy <= 8 && ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg, 1) <= 110 * 1024)
         c.push_back({my, 1});
     for (int t : {8, 16, 32, 64})
         if (t < my && ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy, s->seg) <= 220 * 1024) c.push_back({t, 0});

@@ -7,7 +7,7 @@
 namespace ads {
 
 // device error codes written to a simulation's error word by bounded waits
-enum { kDevErrTimeout = 1, kDevErrAlign = 2 };
+enum { kDevErrTimeout = 1, kDevErrAlign = 2, kDevErrConfig = 3 };
 
 constexpr int kSeg = 32;     // rows per register segment of the line solves ...
 constexpr int kSegAlt = 33;  // ... or 33, when that saves segments (m = 32 s + 1 -> s segments)
@@ -130,6 +130,7 @@ struct ColGroup {
     ColMaps maps[NB];
     ColArgs<T> a[NB];
     int box[NB];
+    int tma[NB];          // mode 1: p, q tiles staged by TMA (else updated in global memory)
     int off[NB + 1];
     int n;
 };

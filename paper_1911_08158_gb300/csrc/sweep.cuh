@@ -370,11 +370,17 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
 //  3. whole plane in the tile: y-direction solve, thread per (x, segment),
 //     results stored from registers to global memory.
 //  4. row tiles only: coalesced store of S1.
-template <typename T, bool PAIR>
+// K1 CTA layouts: one CTA per tile, the 2-CTA cluster pair (FP32), or the
+// wide FP64 CTA for lines of more than 8 segments (every segment of a line
+// needs a warp of its own in the same round).
+enum { kLayoutSingle = 0, kLayoutPair = 1, kLayoutWide = 2 };
+
+template <typename T, int LAYOUT>
 struct RhsThreads {
     // FP64: more registers per thread; a pair CTA holds half a plane, two per SM
-    static constexpr int value = (sizeof(T) == 8 ? 256 : 512) / (PAIR ? 2 : 1);
-    static constexpr int per_sm = PAIR ? 2 : 1;
+    static constexpr int value =
+        LAYOUT == kLayoutWide ? 512 : (sizeof(T) == 8 ? 256 : 512) / (LAYOUT == kLayoutPair ? 2 : 1);
+    static constexpr int per_sm = LAYOUT == kLayoutPair ? 2 : 1;
 };
 
 // index of the simulation that owns block b: off[i] <= b < off[i+1]
@@ -389,10 +395,11 @@ __device__ __forceinline__ int group_find(const int *off, int n, int b)
     return lo;
 }
 
-template <typename T, int P, int NB, int SEG, bool PAIR>
-__global__ void __launch_bounds__(RhsThreads<T, PAIR>::value, RhsThreads<T, PAIR>::per_sm)
+template <typename T, int P, int NB, int SEG, int LAYOUT>
+__global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LAYOUT>::per_sm)
     k_rhs(const __grid_constant__ RhsGroup<T, NB> g)
 {
+    constexpr bool PAIR = LAYOUT == kLayoutPair;
     const int gs = NB > 1 ? group_find(g.off, g.n, blockIdx.x) : 0;
     const RhsArgs<T> &a = g.a[gs];
     const int lb = blockIdx.x - g.off[gs];   // block within this simulation
@@ -422,6 +429,13 @@ __global__ void __launch_bounds__(RhsThreads<T, PAIR>::value, RhsThreads<T, PAIR
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
     const int rows_pad = (tye + 31) & ~31;
     const int cld = q.cld;
+    // every segment of a line needs its own warp in one round; the host never
+    // launches fewer, but a launch that did would compute wrong lines: report it
+    // (all threads of the block, and both CTAs of a pair, take this exit alike)
+    if (nwarps < a.lx.S || (fuse_y && nwarps < a.ly.S)) {
+        if (tid == 0) atomicExch(a.err, kDevErrConfig);
+        return;
+    }
 
     __shared__ __align__(8) uint64_t bar;
     T *S1 = reinterpret_cast<T *>(smem_raw);
@@ -680,7 +694,10 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
     }
     __shared__ __align__(8) uint64_t bar_tab;
     const bool upd = a.mode == 1;
-    const int nch = upd ? (len + box - 1) / box : 0;
+    // update through TMA-staged p, q tiles, or (tiles too large for shared
+    // memory: long FP64 lines) straight from global memory after the solve
+    const bool staged = upd && g.tma[gs];
+    const int nch = staged ? (len + box - 1) / box : 0;
     const int rows = nch * box;
     unsigned char *sm = align128(smem_raw);   // the host reserves 128 spare bytes
     T *bufP = reinterpret_cast<T *>(sm);
@@ -695,11 +712,12 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
     };
     if (tid == 0) {
         mbar_init(&bar_tab, 1);
-        if (upd) mbar_init(&bar, 1);
+        if (staged) mbar_init(&bar, 1);
         fence_mbar_init();
         mbar_expect_tx(&bar_tab, (uint32_t)a.ln.bytes);
         bulk_load(lb, a.ln.base, (uint32_t)a.ln.bytes, &bar_tab);
-        if (upd) {
+        if (upd && blk == 0) a.step[0] += 1;
+        if (staged) {
             mbar_expect_tx(&bar, 2u * nch * 32u * box * sizeof(T));
             for (int c = 0; c < nch; ++c) {
                 int c0, c1, c2;
@@ -707,7 +725,6 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
                 tma_load_3d(bufP + (size_t)c * box * 32, &maps.P, &bar, c0, c1, c2);
                 tma_load_3d(bufQ + (size_t)c * box * 32, &maps.Q, &bar, c0, c1, c2);
             }
-            if (blk == 0) a.step[0] += 1;
         }
     }
     const bool on = x < d.mx && s < a.ln.S;
@@ -729,6 +746,28 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
 #pragma unroll
         for (int k = 0; k < SEG; ++k)
             if (k < n) out[(long long)k * stride] = v[k];
+        return;
+    }
+    if (!staged) {
+        if (!on) return;
+        const T tau2 = a.tau2;
+        T *__restrict__ Pp = a.P + off;
+        T *__restrict__ Qp = a.Q + off;
+#pragma unroll
+        for (int k = 0; k < SEG; ++k) {
+            if (k < n) {
+                const long long o = (long long)k * stride;
+                const T q = Qp[o] + tau2 * v[k];
+                Qp[o] = q;
+                Pp[o] += q;
+            }
+        }
+        if (a.write_a) {
+            T *__restrict__ Ap = a.A + off;
+#pragma unroll
+            for (int k = 0; k < SEG; ++k)
+                if (k < n) Ap[(long long)k * stride] = v[k];
+        }
         return;
     }
     if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, a.err))) return;   // error recorded for the host
@@ -782,9 +821,10 @@ int rhs_blocks(const RhsArgs<T> &a)
 }
 
 // one launch of up to NB simulations, entries a[order[0..n)]
-template <typename T, int P, int NB, int SEG, bool PAIR>
+template <typename T, int P, int NB, int SEG, int LAYOUT>
 cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream_t s)
 {
+    constexpr bool PAIR = LAYOUT == kLayoutPair;
     RhsGroup<T, NB> g;
     std::memset(&g, 0, sizeof(g));
     size_t smem = 0;
@@ -792,6 +832,8 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
     for (int k = 0; k < n; ++k) {
         const RhsArgs<T> &e = a[order[k]];
         if (!rhs_entry_ok(e, SEG) || (e.pair != 0) != PAIR) return cudaErrorInvalidValue;
+        if (std::max(e.lx.S, (PAIR || e.ty == e.d.my) ? e.ly.S : 0) > RhsThreads<T, LAYOUT>::value / 32)
+            return cudaErrorInvalidValue;   // a segment without a warp
         g.a[k] = e;
         g.off[k] = (int)blocks;
         blocks += rhs_blocks(e);
@@ -803,13 +845,13 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
     static size_t smem_set = 48 * 1024;   // per instantiation: opt-in dynamic shared memory
     if (smem > smem_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_rhs<T, P, NB, SEG, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_rhs<T, P, NB, SEG, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
     ++g_launches;
     if (!PAIR) {
-        k_rhs<T, P, NB, SEG, PAIR><<<(unsigned)blocks, RhsThreads<T, PAIR>::value, smem, s>>>(g);
+        k_rhs<T, P, NB, SEG, LAYOUT><<<(unsigned)blocks, RhsThreads<T, LAYOUT>::value, smem, s>>>(g);
         return cudaGetLastError();
     }
     // two CTAs per cluster: the halves of one z-plane (every simulation's
@@ -817,7 +859,7 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)blocks, 1, 1);
-    cfg.blockDim = dim3(RhsThreads<T, PAIR>::value, 1, 1);
+    cfg.blockDim = dim3(RhsThreads<T, LAYOUT>::value, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -827,45 +869,75 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_rhs<T, P, NB, SEG, PAIR>, g);
+    return cudaLaunchKernelEx(&cfg, k_rhs<T, P, NB, SEG, LAYOUT>, g);
 }
 
 // A single simulation is a group of one: one instantiation per (T, P, SEG,
 // pairing) serves both (its parameters are read with a run-time index, which
 // keeps them out of the register budget of the sweeps).  Pairs are FP32 only.
+// A single simulation is a group of one: one instantiation per (T, P, SEG,
+// layout) serves both (its parameters are read with a run-time index, which
+// keeps them out of the register budget of the sweeps).  Pairs are FP32
+// only and need at most 8 segments per line; FP64 lines of more than 8
+// segments take the wide (512-thread) CTA.
+template <typename T>
+int rhs_layout(const RhsArgs<T> &e)
+{
+    if (e.pair) return kLayoutPair;
+    const bool fuse = e.ty == e.d.my;
+    const int smax = std::max(e.lx.S, fuse ? e.ly.S : 0);
+    return (sizeof(T) == 8 && smax > RhsThreads<T, kLayoutSingle>::value / 32) ? kLayoutWide : kLayoutSingle;
+}
+
+template <typename T, int P, int SEG, int LAYOUT>
+cudaError_t rhs_group_chunks(const RhsArgs<T> *a, std::vector<int> &order, cudaStream_t s)
+{
+    // heaviest blocks first (rows x columns of a tile) so that the tail of
+    // the launch holds the short ones
+    auto cost = [&](int i) {
+        const int rows = a[i].pair ? (a[i].d.my + 1) / 2 : a[i].ty;
+        return (long long)rows * a[i].d.mx;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return cost(i) > cost(j); });
+    const int m = (int)order.size();
+    for (int k0 = 0; k0 < m; k0 += kBatch) {
+        cudaError_t e = rhs_group_p<T, P, kBatch, SEG, LAYOUT>(a, order.data() + k0, std::min(kBatch, m - k0), s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 template <typename T, int P>
 cudaError_t rhs_group_dispatch(const RhsArgs<T> *a, int n, cudaStream_t s)
 {
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
         if ((a[i].lx.seg != kSeg && a[i].lx.seg != kSegAlt) || (a[i].pair && sizeof(T) != 4))
             return cudaErrorInvalidValue;
-    for (int pair = 0; pair < 2; ++pair)
+        if (a[i].pair && (a[i].lx.S > 8 || a[i].ly.S > 8)) return cudaErrorInvalidValue;
+    }
+    for (int layout : {kLayoutSingle, kLayoutPair, kLayoutWide})
         for (int seg : {kSeg, kSegAlt}) {
             std::vector<int> order;
             for (int i = 0; i < n; ++i)
-                if (a[i].lx.seg == seg && (a[i].pair != 0) == (pair != 0)) order.push_back(i);
-            // heaviest blocks first (rows x columns of a tile) so that the tail of
-            // the launch holds the short ones
-            auto cost = [&](int i) {
-                const int rows = a[i].pair ? (a[i].d.my + 1) / 2 : a[i].ty;
-                return (long long)rows * a[i].d.mx;
-            };
-            std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return cost(i) > cost(j); });
-            const int m = (int)order.size();
-            for (int k0 = 0; k0 < m; k0 += kBatch) {
-                const int c = std::min(kBatch, m - k0);
-                const int *o = order.data() + k0;
-                cudaError_t e = cudaSuccess;
-                if (pair) {
-                    if constexpr (sizeof(T) == 4)
-                        e = seg == kSeg ? rhs_group_p<T, P, kBatch, kSeg, true>(a, o, c, s)
-                                        : rhs_group_p<T, P, kBatch, kSegAlt, true>(a, o, c, s);
-                } else {
-                    e = seg == kSeg ? rhs_group_p<T, P, kBatch, kSeg, false>(a, o, c, s)
-                                    : rhs_group_p<T, P, kBatch, kSegAlt, false>(a, o, c, s);
-                }
-                if (e != cudaSuccess) return e;
+                if (a[i].lx.seg == seg && rhs_layout(a[i]) == layout) order.push_back(i);
+            if (order.empty()) continue;
+            cudaError_t e = cudaSuccess;
+            if constexpr (sizeof(T) == 4) {
+                if (layout == kLayoutWide) return cudaErrorInvalidValue;
+                e = layout == kLayoutPair
+                        ? (seg == kSeg ? rhs_group_chunks<T, P, kSeg, kLayoutPair>(a, order, s)
+                                       : rhs_group_chunks<T, P, kSegAlt, kLayoutPair>(a, order, s))
+                        : (seg == kSeg ? rhs_group_chunks<T, P, kSeg, kLayoutSingle>(a, order, s)
+                                       : rhs_group_chunks<T, P, kSegAlt, kLayoutSingle>(a, order, s));
+            } else {
+                if (layout == kLayoutPair) return cudaErrorInvalidValue;
+                e = layout == kLayoutWide
+                        ? (seg == kSeg ? rhs_group_chunks<T, P, kSeg, kLayoutWide>(a, order, s)
+                                       : rhs_group_chunks<T, P, kSegAlt, kLayoutWide>(a, order, s))
+                        : (seg == kSeg ? rhs_group_chunks<T, P, kSeg, kLayoutSingle>(a, order, s)
+                                       : rhs_group_chunks<T, P, kSegAlt, kLayoutSingle>(a, order, s));
             }
+            if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
 }
@@ -895,10 +967,16 @@ cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *ord
         const int outer = e.axis == 1 ? e.d.mz : e.d.my;
         const int box = col_box(len);
         size_t tiles = 0;
+        g.tma[k] = 0;
         if (e.mode == 1) {
-            if (maps) g.maps[k] = maps[i];
-            else if (!make_update_maps(&g.maps[k], e.P, e.Q, sizeof(T), e.d, e.axis)) return cudaErrorInvalidValue;
             tiles = 2 * (size_t)((len + box - 1) / box) * box * 32 * sizeof(T);
+            if (128 + tiles + col_smem_bytes(P, sizeof(T), len, e.ln.S, SEG) <= 200 * 1024) {
+                if (maps) g.maps[k] = maps[i];
+                else if (!make_update_maps(&g.maps[k], e.P, e.Q, sizeof(T), e.d, e.axis)) return cudaErrorInvalidValue;
+                g.tma[k] = 1;
+            } else {
+                tiles = 0;   // update from global memory
+            }
         }
         g.a[k] = e;
         g.box[k] = box;
