@@ -68,3 +68,43 @@ def test_zero_steps_and_empty_batch():
     assert sim.step_count == 0
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_elasticity_long_lines(precision):
+    """Diagonal-block sweeps of more than 8 segments (wide FP64 CTA)."""
+    from tests.cases import assert_parity, gpu_elastic, oracle_elastic
+    case = wl.elastic_case(ne=(300, 4, 3), p=2, tau=4e-3, steps=6, seed=5, sigma=0.1)
+    ref = oracle_elastic(case, 6)[6]
+    _, got = gpu_elastic(case, 6, precision)
+    assert_parity(got[6][0], ref[0], TOL[precision] * (2 if precision == "fp64" else 1), "U %s" % precision)
+
+
+@pytest.mark.parametrize("boundary", ["dirichlet", "natural"])
+def test_2d_long_lines_fp64(boundary):
+    case = wl.ricker_case(ne=(3, 509, 0), p=3, tau=2e-3, steps=10, seed=3, sigma=0.05)
+    ref = oracle_wave(case, 10, boundary=boundary)[10]
+    from paper_1911_08158_gb300 import Simulation
+    sim = Simulation(case.n_elem, case.p, case.tau, precision="fp64", boundary=boundary)
+    sim.set_source(case.source)
+    sim.set_gaussian_state(None, None)
+    sim.step(10)
+    check_state(sim.get_state(), ref, "fp64", case.tau, 2e-12, "2D %s" % boundary)
+
+
+def test_batch_mixing_wide_and_narrow_fp64():
+    from paper_1911_08158_gb300 import Simulation, batch_step
+    cases = [wl.ricker_case(ne=(300, 3, 2), p=2, tau=2e-3, steps=0, seed=1, sigma=0.05),
+             wl.ricker_case(ne=(10, 9, 8), p=2, tau=2e-3, steps=0, seed=2, sigma=0.05)]
+    alone = [gpu_wave(c, 17, "fp64")[1][17] for c in cases]
+    sims = []
+    for c in cases:
+        s = Simulation(c.n_elem, c.p, c.tau, precision="fp64")
+        s.set_source(c.source)
+        s.set_gaussian_state(None, None)
+        sims.append(s)
+    batch_step(sims, 17)
+    for s, ref in zip(sims, alone):
+        got = s.get_state()
+        for k in range(3):
+            assert np.array_equal(got[k], ref[k])
