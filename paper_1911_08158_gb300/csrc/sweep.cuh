@@ -174,12 +174,21 @@ __device__ __forceinline__ void carry_bwd(const T *Psi, int S, int s, const T *C
     }
 }
 
+// Barrier of the warps that share lines: the whole block (id 0), or a named
+// barrier of `nthreads` threads (the S warps of one line group).
+__device__ __forceinline__ void group_sync(int id, int nthreads)
+{
+    if (id == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Passes 2-3 with the two carry exchanges, after pass 1 left v in
-// registers.  All threads of the block call it (it synchronises); `on`
-// marks threads that own a segment.  CT/CH: [S][P][ld], slot j.
+// registers.  Every thread of the synchronising group calls it (barrier id
+// 0: the whole block; else the named barrier of one line group); `on` marks
+// threads that own a segment.  CT/CH: [S][P][ld], slot j.
 template <typename T, int P, int SEG>
 __device__ __forceinline__ void seg_finish(const LineSm<T> &L, bool on, int s, int j, int ld, T *CT, T *CH,
-                                           T (&v)[SEG])
+                                           T (&v)[SEG], int bar_id = 0, int bar_threads = 0)
 {
     constexpr int W = 2 * P + 1;
     const int b0 = s * SEG;
@@ -187,7 +196,7 @@ __device__ __forceinline__ void seg_finish(const LineSm<T> &L, bool on, int s, i
 #pragma unroll
         for (int k = 0; k < P; ++k) CT[(s * P + k) * ld + j] = v[SEG - 1 - k];
     }
-    __syncthreads();
+    group_sync(bar_id, bar_threads);
     if (on) {
         T c[P];
         carry_fwd<T, P>(L.Phi, s, CT, ld, j, c);
@@ -195,7 +204,7 @@ __device__ __forceinline__ void seg_finish(const LineSm<T> &L, bool on, int s, i
 #pragma unroll
         for (int k = 0; k < P; ++k) CH[(s * P + k) * ld + j] = v[k];
     }
-    __syncthreads();
+    group_sync(bar_id, bar_threads);
     if (on) {
         T e[P];
         carry_bwd<T, P>(L.Psi, L.S, s, CH, ld, j, e);
@@ -537,13 +546,17 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
     }
 
     // ---- phase 2: x-direction, thread per (row, segment); rounds of row groups
+    // line groups (32 rows x S segments, S warps) run their rounds
+    // independently: each synchronises on a named barrier of its own (ids
+    // 1..15); rows and carry slots of different groups never overlap
     const int RG = rows_pad >> 5;
-    const int gpr2 = nwarps / LX.S > 0 ? nwarps / LX.S : 1;
+    const int gpr2 = min(nwarps / LX.S, 15);
     for (int g0 = 0; g0 < RG; g0 += gpr2) {
         const int gi = warp / LX.S, s = warp % LX.S;
         const int g = g0 + gi;
+        if (gi >= gpr2 || g >= RG) continue;   // the whole group skips alike
         const int l = g * 32 + lane;
-        const bool on = gi < gpr2 && g < RG && l < tye;
+        const bool on = l < tye;
         const int b0 = s * SEG;
         const int n = on ? min(SEG, mx - b0) : 0;
         T v[SEG];
@@ -584,15 +597,16 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
             else
                 phase2_fwd<T, P, SEG, kSegGeneral>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
         }
-        seg_finish<T, P, SEG>(LX, on, s, l, cld, CT, CH, v);   // reads of S1/S2 are done (its first barrier)
+        // the group's reads of its S1/S2 rows are done at seg_finish's first barrier
+        seg_finish<T, P, SEG>(LX, on, s, l, cld, CT, CH, v, 1 + gi, 32 * LX.S);
         if (on) {
             T *row1 = S1 + (size_t)l * RS;
 #pragma unroll
             for (int k = 0; k < SEG; ++k)
                 if (k < n) row1[b0 + k] = v[k];
         }
-        __syncthreads();
     }
+    __syncthreads();   // phase 3 reads every row
 
     // ---- phase 3: y-direction (whole plane), thread per (x, segment); rounds of column groups
     if (fuse_y) {
@@ -612,12 +626,13 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
         }
         const int ycut = PAIR ? q.ycut : my;
         const int CG = (c1 - c0 + 31) >> 5;
-        const int gpr3 = nwarps / LY.S > 0 ? nwarps / LY.S : 1;
+        const int gpr3 = min(nwarps / LY.S, 15);
         for (int g0 = 0; g0 < CG; g0 += gpr3) {
             const int gi = warp / LY.S, s = warp % LY.S;
+            if (gi >= gpr3 || g0 + gi >= CG) continue;   // the whole column group skips alike
             const int xl = (g0 + gi) * 32 + lane;   // column slot within this CTA's range
             const int x = c0 + xl;
-            const bool on = gi < gpr3 && x < c1;
+            const bool on = x < c1;
             const int b0 = s * SEG;
             const int n = on ? min(SEG, my - b0) : 0;
             T v[SEG];
@@ -632,7 +647,7 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
                 for (int k = 0; k < SEG; ++k) v[k] = (k < n) ? S1[(size_t)(b0 + k) * RS + x] : T(0);
             }
             if (on) seg_pass1<T, P, SEG>(LY.fac + b0 * W, v);
-            seg_finish<T, P, SEG>(LY, on, s, xl, cld, CT, CH, v);
+            seg_finish<T, P, SEG>(LY, on, s, xl, cld, CT, CH, v, 1 + gi, 32 * LY.S);
             // finished columns go straight to global memory (lanes = consecutive
             // x: one coalesced row segment per k); the next round reads other
             // columns of S1 and its carry writes follow seg_finish's barriers
