@@ -259,19 +259,25 @@ __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int
     for (int k = 0; k < W; ++k) r1[k] = r2[k] = V2{T(0), T(0)};
     const int n = ye - yb + 2 * P;
     const T *rowp = col0 + (long long)(yb - P) * sx;
+    // the W plane values of stream row r (zero outside the grid or past the chunk)
+    auto load_row = [&](int r, V2(&dst)[W]) {
+        const int yp = yb - P + r;
+        const bool ok = GUARD ? ((r < n) && yp >= 0 && yp < my) : (r < n);
+        const T *c = rowp + (long long)r * sx;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const bool okk = GUARD ? (ok && zok[k]) : ok;
+            dst[k] = okk ? *reinterpret_cast<const V2 *>(c + (long long)k * plane) : V2{T(0), T(0)};
+        }
+    };
+    V2 v[W];   // current row; the next row's loads are issued before it is contracted
+    load_row(0, v);
     for (int r0 = 0; r0 < n; r0 += W) {
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             const int r = r0 + j;
-            const int yp = yb - P + r;
-            const bool ok = GUARD ? ((r < n) && yp >= 0 && yp < my) : (r < n);
-            const T *c = rowp + (long long)r * sx;
-            V2 v[W];
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const bool okk = GUARD ? (ok && zok[k]) : ok;
-                v[k] = okk ? *reinterpret_cast<const V2 *>(c + (long long)k * plane) : V2{T(0), T(0)};
-            }
+            V2 nv[W];
+            load_row(r + 1, nv);
             V2 t1 = V2{T(0), T(0)}, t2 = V2{T(0), T(0)};
 #pragma unroll
             for (int k = 0; k < W; ++k) {
@@ -304,6 +310,8 @@ __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int
                 s2col[(size_t)y * RS] = c.x;
                 s2col[(size_t)y * RS + 1] = c.y;
             }
+#pragma unroll
+            for (int k = 0; k < W; ++k) v[k] = nv[k];
         }
     }
 }
