@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -998,10 +999,36 @@ struct BatchRes {
 constexpr int kBatchChunk = 16;        // steps per captured batch graph
 constexpr size_t kBatchGraphs = 16;    // cached batch graphs per device
 
+// Batch streams, graphs and the tuning cache are process-wide: one mutex
+// serialises the host-side work of ads_batch_step, ads_autotune and the
+// graph clean-up of ads_destroy across host threads.
+std::mutex &batch_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+
 BatchRes &batch_res(int device)
 {
     static std::map<int, BatchRes> res;
     return res[device];
+}
+
+// drop cached batch graphs that hold a simulation about to be destroyed
+void forget_batch_graphs(const ads_sim *s)
+{
+    std::lock_guard<std::mutex> lock(batch_mutex());
+    BatchRes &br = batch_res(s->device);
+    for (auto it = br.graphs.begin(); it != br.graphs.end();) {
+        bool holds = false;
+        for (const auto &id : it->first.ids) holds = holds || id.first == s->uid;
+        if (holds) {
+            cudaGraphExecDestroy(it->second.exec);
+            it = br.graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
 }
 
 int group_stream(BatchRes &br, int prec, int p, cudaStream_t *out)
@@ -1072,6 +1099,7 @@ int batch_graph(BatchRes &br, const std::vector<ads_sim *> &g, cudaStream_t st, 
 int batch_groups(std::map<std::pair<int, int>, std::vector<ads_sim *>> &groups, int nsteps)
 {
     if (groups.empty()) return ADS_OK;
+    std::lock_guard<std::mutex> lock(batch_mutex());
     BatchRes &br = batch_res(groups.begin()->second[0]->device);
     std::vector<cudaEvent_t> evs;
     auto new_event = [&](cudaEvent_t *e) -> int {
@@ -1176,6 +1204,7 @@ void set_tile(ads_sim *s, std::pair<int, int> t)
 // kind) for the process.
 int autotune(ads_sim *s, int trial_steps)
 {
+    std::lock_guard<std::mutex> lock(batch_mutex());
     const TuneKey key{s->d.mx, s->d.my, s->d.mz, s->p, s->prec, s->kind};
     auto hit = tune_cache().find(key);
     if (hit != tune_cache().end()) {
@@ -1454,7 +1483,7 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
         if (q) cudaMemsetAsync(q, 0, q == s->U || q == s->Up || q == s->R || q == s->Y ? 3 * n : n, s->stream);
     cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->stream);
     cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
-    static unsigned long long next_uid = 0;
+    static std::atomic<unsigned long long> next_uid{0};
     s->uid = ++next_uid;
     if (s->kind == ADS_SCALAR_WAVE)
         s->has_maps = ads::make_update_maps(&s->upd_maps, s->P, s->Q, (int)elem(s), s->d, 2);
@@ -1471,6 +1500,7 @@ void ads_destroy(ads_sim_t *s)
     if (!s) return;
     cudaSetDevice(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->uid) forget_batch_graphs(s);
     for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
     std::vector<void *> ptrs;
     for (auto &kv : s->live) ptrs.push_back(kv.first);

@@ -15,7 +15,7 @@
 
 namespace ads {
 
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
 
 namespace {
 

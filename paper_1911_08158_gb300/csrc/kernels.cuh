@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace ads {
 
 // device error codes written to a simulation's error word by bounded waits
@@ -244,6 +246,7 @@ cudaError_t launch_delay(unsigned long long ns, cudaStream_t s);
 // bounded-wait self-test: err[0] = timeout code if the wait ran out, err[1] = 1 if it completed
 cudaError_t launch_wait_selftest(long long cycles, int *err, cudaStream_t s);
 
-extern unsigned long long g_launches;
+// kernel launches issued by the library (all host threads)
+extern std::atomic<unsigned long long> g_launches;
 
 }  // namespace ads
