@@ -178,3 +178,37 @@ def test_batch_rejects_bad_arguments():
         batch_step([s, s], 1)
     with pytest.raises(AdsError):
         batch_step([s], -1)
+
+
+def test_concurrent_host_threads():
+    """Two host threads drive their own batches at the same time (separate
+    simulations and streams); each result equals the sequential run."""
+    import threading
+    from paper_1911_08158_gb300 import batch_step
+    cases = [_mixed_cases()[i] for i in (0, 1, 2, 3)]
+    seq = []
+    for c in cases:
+        s = _make(c, "fp32")
+        s.step(23)
+        seq.append(s.get_state()[0])
+        s.close()
+    sims = [_make(c, "fp32") for c in cases]
+    errors = []
+
+    def work(members):
+        try:
+            for _ in range(23):
+                batch_step(members, 1)
+            for m in members:
+                m.sync()
+        except Exception as e:   # noqa: BLE001
+            errors.append(e)
+
+    ts = [threading.Thread(target=work, args=(sims[:2],)), threading.Thread(target=work, args=(sims[2:],))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors
+    for s, ref in zip(sims, seq):
+        assert np.array_equal(s.get_state()[0], ref)
