@@ -110,6 +110,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """The largest value of x over the ranks of the process group (the job
+    takes as long as its slowest replica); x itself for one process."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, ws: int, t_max: float) -> float:
+    """Whole-job throughput of ws independent replicas (weak scaling): all
+    ranks' units over the slowest rank's time."""
+    return units_per_rank * ws / t_max
+
+
 def make_sims(precision, torch, ads, wl, stream=None):
     sims = []
     for p in PS:
@@ -174,13 +193,8 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - wall0
     launches = ads.launch_count() - l0
-    t_dev = float(sum(times))
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    value = dof_steps * args.steps * ws / t_dev
+    t_dev = max_over_ranks(float(sum(times)), ws)
+    value = replica_value(dof_steps * args.steps, ws, t_dev)
 
     # ---- per-kernel times (CUDA events between the kernels of single steps)
     kt = {}
@@ -394,13 +408,18 @@ def run_elastic(args, stream, flush):
 
 
 def run_serving(args):
+    """The request stream of the serving configuration; with N ranks each GPU
+    serves its shard of whole requests (no communication) and rank 0 reports
+    its own latencies."""
     from paper_1911_08158_gb300 import workloads as wl
-    from paper_1911_08158_gb300.serve import Server
+    from paper_1911_08158_gb300.serve import Server, shard_requests
+    ws, rank, _ = dist_env()
     reqs = wl.serving_requests(count=args.serve_requests, rate=20.0, seed=0)
-    rep = Server(150 * 10 ** 9, precision="fp32", chunk=16).run(reqs)
+    mine = shard_requests(reqs, rank, ws)
+    rep = Server(150 * 10 ** 9, precision="fp32", chunk=16).run(mine)
     out = rep.summary()
     out.update(workload="serving_poisson20_%dreq_wave80_elastic20_24to256_budget150GB_fp32" % len(reqs),
-               unit_latency="s")
+               unit_latency="s", shard="rank %d of %d: %d requests" % (rank, ws, len(mine)))
     return out
 
 

@@ -31,6 +31,24 @@ def request_dofs(req) -> int:
     return int(np.prod([n + req.p for n in req.n_elem])) * comps
 
 
+def shard_requests(requests, rank: int, world: int):
+    """Requests of one rank when a stream is served by `world` independent
+    GPUs (whole simulations per GPU, no communication): greedy assignment in
+    arrival order to the rank with the least DOF-steps so far.  Every rank
+    computes the same assignment, so the shards are disjoint and cover the
+    stream."""
+    if world <= 1:
+        return list(requests)
+    load = [0] * world
+    mine = []
+    for r in sorted(requests, key=lambda r: (r.arrival, r.rid)):
+        k = min(range(world), key=lambda i: (load[i], i))
+        load[k] += request_dofs(r) * int(r.steps)
+        if k == rank:
+            mine.append(r)
+    return mine
+
+
 def make_simulation(req, precision="fp32"):
     """Library simulation of a request: zero initial state, the request's
     Ricker x Gaussian source (vector direction for elasticity)."""
