@@ -6,7 +6,9 @@
  *   - space: tensor-product B-splines of degree p on [0,L0]x[0,L1]x[0,L2],
  *     open uniform knots, n_a = n_elem[a] + p functions per axis (Sec. 2);
  *     homogeneous Dirichlet boundary (the first and last function per axis
- *     are fixed at zero);
+ *     are fixed at zero) or the natural (traction-free) boundary of Sec. 5
+ *     (ads_grid_t.boundary); n_elem[2] = 0 makes a 2D problem on
+ *     [0,L0]x[0,L1] (one constant function along z, n_2 = 1);
  *   - scalar wave u_tt - c2 Lap u = f (Sec. 2): implicit Newmark step with
  *     the Kronecker split operator (eq. pwave2)
  *         (Mx+eta Kx)(x)(My+eta Ky)(x)(Mz+eta Kz) a_{n+1}
@@ -24,8 +26,9 @@
  *   - Return ADS_OK (0) or a negative ADS_ERR_* code; ads_last_error() gives
  *     a message (thread-local, valid until the next call on that thread).
  *   - Field arrays cross the boundary as FP64 coefficient arrays of the FULL
- *     space, [comp][z][y][x] with x fastest, count = comps*n0*n1*n2 doubles;
- *     boundary coefficients are ignored on input and zero on output.
+ *     space, [comp][z][y][x] with x fastest, count = comps*n0*n1*n2 doubles
+ *     (n from ads_dims); with the Dirichlet restriction the boundary
+ *     coefficients are ignored on input and zero on output.
  *   - mem = ADS_HOST: plain host pointers (pageable or pinned); the caller
  *     owns them, the library copies and keeps no reference.
  *     mem = ADS_DEVICE: device pointers on the simulation's device.
@@ -34,7 +37,9 @@
  *     or from cudaMalloc.
  *   - Work is ordered on the simulation's CUDA stream; ads_step returns
  *     without waiting, ads_get_state / ads_energy / ads_sync wait.
- *   - A simulation is not thread-safe: one caller thread at a time.
+ *   - A simulation is not thread-safe: one caller thread at a time.  Distinct
+ *     simulations may be driven from distinct threads (ads_batch_step and
+ *     ads_autotune serialise their shared process-wide state).
  */
 #ifndef ADS_H
 #define ADS_H
@@ -134,7 +139,8 @@ typedef struct {
  * opts may be NULL (FP64, current device, library stream, cudaMalloc).
  * State starts at zero with step counter 0.  Errors: INVALID_ARG (sizes,
  * tau, material), UNSUPPORTED (p, or a grid beyond the kernels' limits:
- * n_elem + p - 2 <= 512 per axis), OOM, CUDA. */
+ * at most 512 unknowns per axis: n_elem + p - 2, or n_elem + p with the
+ * natural boundary), OOM, CUDA. */
 int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *mat,
                const ads_options_t *opts, ads_sim_t **out);
 
