@@ -1167,7 +1167,7 @@ std::vector<std::pair<int, int>> tile_candidates(const ads_sim *s)
     const int Sx = segs(s, s->d.mx), Sy = segs(s, s->d.my), my = s->d.my;
     std::vector<std::pair<int, int>> c;
     if (ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg) <= 220 * 1024) c.push_back({my, 0});
-    if (el == 4 && my >= 2 && Sx <= 8 && Sy <= 8 && ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg, 1) <= 110 * 1024)
+    if (el == 4 && my >= 2 && Sx <= 8 && Sy <= 8 && s->seg != ads::kSegLong && ads::rhs_smem_bytes(s->p, el, s->d, my, Sx, Sy, s->seg, 1) <= 110 * 1024)
         c.push_back({my, 1});
     for (int t : {8, 16, 32, 64})
         if (t < my && ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy, s->seg) <= 220 * 1024) c.push_back({t, 0});
@@ -1423,7 +1423,8 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     s->d.offz = plane2d ? 0 : s->d.off;
     {
         const int m3[3] = {s->d.mx, s->d.my, s->d.mz};
-        s->seg = ads::choose_seg(m3);   // 33-row segments when they save segments (m = 32 s + 1)
+        // 33-row segments when they save segments (m = 32 s + 1), 44 when they save K1 rounds
+        s->seg = ads::choose_seg(m3, s->prec == ADS_FP64 ? 8 : 4);
     }
     choose_tiles(s);
     if (o.tile_lines > 0) {
@@ -1946,7 +1947,7 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
         m[a] = (size_t)me;
         mi[a] = (int)me;
     }
-    const int seg = ads::choose_seg(mi);
+    const int seg = ads::choose_seg(mi, precision == ADS_FP64 ? 8 : 4);
     for (int a = 0; a < 3; ++a) {
         S[a] = (m[a] + seg - 1) / seg;
         mp[a] = S[a] * seg;

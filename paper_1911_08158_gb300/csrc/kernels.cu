@@ -486,14 +486,38 @@ size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, in
     return n * elem + 16 + ((rhs_image_elems(p, d, Sx, Sy, seg) * elem + 15) & ~(size_t)15);
 }
 
-int choose_seg(const int *m)
+namespace {
+// rounds of line groups (32 lines x S segment warps) in a CTA of `warps` warps
+int line_rounds(int lines, int S, int warps)
+{
+    const int per = warps / S;
+    if (per < 1) return 1 << 20;
+    const int groups = (lines + 31) / 32;
+    return (groups + per - 1) / per;
+}
+}  // namespace
+
+int choose_seg(const int *m, int elem)
 {
     int n32 = 0, n33 = 0;
     for (int a = 0; a < 3; ++a) {
         n32 += (m[a] + kSeg - 1) / kSeg;
         n33 += (m[a] + kSegAlt - 1) / kSegAlt;
     }
-    return n33 < n32 ? kSegAlt : kSeg;
+    int best = n33 < n32 ? kSegAlt : kSeg;
+    // K1 (whole plane per CTA) runs the x sweep over my lines and the y sweep
+    // over mx lines, line groups in rounds; a round lasts about one segment
+    // of recurrences.  m = 129 (128 elements, p = 3): 33-row segments need
+    // two rounds per sweep, 44-row segments one.
+    const int warps = rhs_threads(elem) / 32;
+    auto cost = [&](int seg) {
+        const int Sx = (m[0] + seg - 1) / seg, Sy = (m[1] + seg - 1) / seg;
+        if (Sx > 16 || Sy > 16) return 1 << 30;
+        return seg * (line_rounds(m[1], Sx, warps) + line_rounds(m[0], Sy, warps));
+    };
+    const int Sz = (m[2] + kSegLong - 1) / kSegLong;
+    if (Sz <= 16 && cost(kSegLong) < cost(best)) best = kSegLong;
+    return best;
 }
 
 int rhs_threads(int elem) { return elem == 8 ? 256 : 512; }
@@ -515,16 +539,36 @@ size_t col_smem_bytes(int p, int elem, int len, int S, int seg)
     }
 
 template <typename T>
+cudaError_t launch_rhs_group(int p, const RhsArgs<T> *a, int n, cudaStream_t s)
+{
+    if (!a || n <= 0 || p < 1 || p > 4) return cudaErrorInvalidValue;
+    bool has[3] = {false, false, false};
+    for (int i = 0; i < n; ++i) {
+        const int seg = a[i].lx.seg;
+        if (!seg_supported(seg)) return cudaErrorInvalidValue;
+        // the cluster pair: FP32, at most 8 segments per line, 32- or 33-row segments
+        if (a[i].pair && (sizeof(T) != 4 || a[i].lx.S > 8 || a[i].ly.S > 8 || seg == kSegLong))
+            return cudaErrorInvalidValue;
+        has[seg == kSeg ? 0 : seg == kSegAlt ? 1 : 2] = true;
+    }
+    cudaError_t e = cudaSuccess;
+    if (has[0] && (e = launch_rhs_seg<T, kSeg>(p, a, n, s)) != cudaSuccess) return e;
+    if (has[1] && (e = launch_rhs_seg<T, kSegAlt>(p, a, n, s)) != cudaSuccess) return e;
+    if (has[2] && (e = launch_rhs_seg<T, kSegLong>(p, a, n, s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+template <typename T>
 cudaError_t launch_rhs(int p, int seg, const RhsArgs<T> &a, cudaStream_t s)
 {
-    if (seg != kSeg && seg != kSegAlt) return cudaErrorInvalidValue;
+    if (!seg_supported(seg)) return cudaErrorInvalidValue;
     return launch_rhs_group<T>(p, &a, 1, s);
 }
 
 template <typename T>
 cudaError_t launch_col(int p, int seg, const ColArgs<T> &a, cudaStream_t s)
 {
-    if (seg != kSeg && seg != kSegAlt) return cudaErrorInvalidValue;
+    if (!seg_supported(seg)) return cudaErrorInvalidValue;
     return launch_col_group<T>(p, &a, nullptr, 1, s);
 }
 
@@ -731,6 +775,7 @@ cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long 
 
 #define ADS_INST(T)                                                                                                \
     template cudaError_t launch_rhs<T>(int, int, const RhsArgs<T> &, cudaStream_t);                                \
+    template cudaError_t launch_rhs_group<T>(int, const RhsArgs<T> *, int, cudaStream_t);                         \
     template cudaError_t launch_col<T>(int, int, const ColArgs<T> &, cudaStream_t);                                \
     template cudaError_t launch_axis_apply<T>(int, const T *, int, const T *, T *, Dims, T, T, int, cudaStream_t); \
     template cudaError_t launch_solve_x<T>(int, const T *, T *, Dims, cudaStream_t);                               \

@@ -11,8 +11,10 @@ namespace ads {
 // device error codes written to a simulation's error word by bounded waits
 enum { kDevErrTimeout = 1, kDevErrAlign = 2, kDevErrConfig = 3 };
 
-constexpr int kSeg = 32;     // rows per register segment of the line solves ...
-constexpr int kSegAlt = 33;  // ... or 33, when that saves segments (m = 32 s + 1 -> s segments)
+constexpr int kSeg = 32;      // rows per register segment of the line solves ...
+constexpr int kSegAlt = 33;   // ... or 33, when that saves segments (m = 32 s + 1 -> s segments) ...
+constexpr int kSegLong = 44;  // ... or 44, when 3 segments let every line group of a plane run at once (m <= 132)
+inline bool seg_supported(int seg) { return seg == kSeg || seg == kSegAlt || seg == kSegLong; }
 constexpr int kBatch = 32;   // simulations per grouped launch
 
 // Interior field layout on the device: [z][y][x], x fastest, row pitch sx
@@ -37,7 +39,7 @@ struct LineDev {
     const T *base;
     int S;
     int bytes;            // padded to 16
-    int seg;              // rows per segment (kSeg or kSegAlt)
+    int seg;              // rows per segment (kSeg, kSegAlt or kSegLong)
 };
 
 // Operator band of one axis with its Toeplitz interior rows [lo, hi).
@@ -144,9 +146,11 @@ int rhs_threads(int elem);
 size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy, int seg);
 size_t line_image_elems(int p, int S, int seg);
 size_t col_smem_bytes(int p, int elem, int len, int S, int seg);
-// segment length for a space with interior sizes m[3]: kSegAlt when it
-// needs fewer segments in all than kSeg
-int choose_seg(const int *m);
+// segment length for a space with interior sizes m[3] and elements of
+// elem bytes: kSegAlt when it needs fewer segments in all than kSeg;
+// kSegLong when it needs fewer rounds of line groups in K1 (measured in
+// rows of dependent recurrence: rounds x segment length)
+int choose_seg(const int *m, int elem);
 
 template <typename T>
 cudaError_t launch_rhs(int p, int seg, const RhsArgs<T> &a, cudaStream_t s);
@@ -157,6 +161,9 @@ cudaError_t launch_col(int p, int seg, const ColArgs<T> &a, cudaStream_t s);
 // per entry (mode 1), else they are encoded here.
 template <typename T>
 cudaError_t launch_rhs_group(int p, const RhsArgs<T> *a, int n, cudaStream_t s);
+// the entries of a[0..n) whose segment length is SEG (one translation unit each)
+template <typename T, int SEG>
+cudaError_t launch_rhs_seg(int p, const RhsArgs<T> *a, int n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s);
 

@@ -246,7 +246,9 @@ __device__ __forceinline__ double2 fma2(double a, double2 b, double2 c)
     return make_double2(fma(a, b.x, c.x), fma(a, b.y, c.y));
 }
 
-template <typename T, int P, bool GUARD, bool INTERIOR>
+constexpr int kPhase1Lookahead = 1;   // stream rows whose loads are in flight ahead of the one contracted
+
+template <typename T, int P, bool GUARD, bool INTERIOR, int PF = kPhase1Lookahead>
 __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int sx, int my, const bool (&zok)[2 * P + 1],
                                              const T (&cm)[2 * P + 1], const T (&ck)[2 * P + 1],
                                              const T (&mym)[2 * P + 1], const T (&myk)[2 * P + 1], const T *bMy,
@@ -270,14 +272,17 @@ __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int
             dst[k] = okk ? *reinterpret_cast<const V2 *>(c + (long long)k * plane) : V2{T(0), T(0)};
         }
     };
-    V2 v[W];   // current row; the next row's loads are issued before it is contracted
-    load_row(0, v);
+    // rows r .. r+PF-1 in flight: row r+PF's loads are issued before row r is contracted
+    V2 pf[PF][W];
+#pragma unroll
+    for (int d = 0; d < PF; ++d) load_row(d, pf[d]);
     for (int r0 = 0; r0 < n; r0 += W) {
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             const int r = r0 + j;
             V2 nv[W];
-            load_row(r + 1, nv);
+            load_row(r + PF, nv);
+            const V2(&v)[W] = pf[0];
             V2 t1 = V2{T(0), T(0)}, t2 = V2{T(0), T(0)};
 #pragma unroll
             for (int k = 0; k < W; ++k) {
@@ -311,7 +316,11 @@ __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int
                 s2col[(size_t)y * RS + 1] = c.y;
             }
 #pragma unroll
-            for (int k = 0; k < W; ++k) v[k] = nv[k];
+            for (int d = 0; d + 1 < PF; ++d)
+#pragma unroll
+                for (int k = 0; k < W; ++k) pf[d][k] = pf[d + 1][k];
+#pragma unroll
+            for (int k = 0; k < W; ++k) pf[PF - 1][k] = nv[k];
         }
     }
 }
@@ -930,38 +939,28 @@ cudaError_t rhs_group_chunks(const RhsArgs<T> *a, std::vector<int> &order, cudaS
     return cudaSuccess;
 }
 
-template <typename T, int P>
-cudaError_t rhs_group_dispatch(const RhsArgs<T> *a, int n, cudaStream_t s)
+// the entries of segment length SEG, one grouped launch series per layout;
+// 44-row segments take the single-CTA layout only
+template <typename T, int P, int SEG>
+cudaError_t rhs_seg_p(const RhsArgs<T> *a, int n, cudaStream_t s)
 {
-    for (int i = 0; i < n; ++i) {
-        if ((a[i].lx.seg != kSeg && a[i].lx.seg != kSegAlt) || (a[i].pair && sizeof(T) != 4))
-            return cudaErrorInvalidValue;
-        if (a[i].pair && (a[i].lx.S > 8 || a[i].ly.S > 8)) return cudaErrorInvalidValue;
-    }
-    for (int layout : {kLayoutSingle, kLayoutPair, kLayoutWide})
-        for (int seg : {kSeg, kSegAlt}) {
-            std::vector<int> order;
-            for (int i = 0; i < n; ++i)
-                if (a[i].lx.seg == seg && rhs_layout(a[i]) == layout) order.push_back(i);
-            if (order.empty()) continue;
-            cudaError_t e = cudaSuccess;
+    for (int layout : {kLayoutSingle, kLayoutPair, kLayoutWide}) {
+        std::vector<int> order;
+        for (int i = 0; i < n; ++i)
+            if (a[i].lx.seg == SEG && rhs_layout(a[i]) == layout) order.push_back(i);
+        if (order.empty()) continue;
+        cudaError_t e = cudaErrorInvalidValue;
+        if (layout == kLayoutSingle) {
+            e = rhs_group_chunks<T, P, SEG, kLayoutSingle>(a, order, s);
+        } else if constexpr (SEG != kSegLong) {
             if constexpr (sizeof(T) == 4) {
-                if (layout == kLayoutWide) return cudaErrorInvalidValue;
-                e = layout == kLayoutPair
-                        ? (seg == kSeg ? rhs_group_chunks<T, P, kSeg, kLayoutPair>(a, order, s)
-                                       : rhs_group_chunks<T, P, kSegAlt, kLayoutPair>(a, order, s))
-                        : (seg == kSeg ? rhs_group_chunks<T, P, kSeg, kLayoutSingle>(a, order, s)
-                                       : rhs_group_chunks<T, P, kSegAlt, kLayoutSingle>(a, order, s));
+                if (layout == kLayoutPair) e = rhs_group_chunks<T, P, SEG, kLayoutPair>(a, order, s);
             } else {
-                if (layout == kLayoutPair) return cudaErrorInvalidValue;
-                e = layout == kLayoutWide
-                        ? (seg == kSeg ? rhs_group_chunks<T, P, kSeg, kLayoutWide>(a, order, s)
-                                       : rhs_group_chunks<T, P, kSegAlt, kLayoutWide>(a, order, s))
-                        : (seg == kSeg ? rhs_group_chunks<T, P, kSeg, kLayoutSingle>(a, order, s)
-                                       : rhs_group_chunks<T, P, kSegAlt, kLayoutSingle>(a, order, s));
+                if (layout == kLayoutWide) e = rhs_group_chunks<T, P, SEG, kLayoutWide>(a, order, s);
             }
-            if (e != cudaSuccess) return e;
         }
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
@@ -1027,18 +1026,18 @@ cudaError_t col_group_dispatch(const ColArgs<T> *a, const ColMaps *maps, int n, 
 {
     auto len = [&](int i) { return a[i].axis == 1 ? a[i].d.my : a[i].d.mz; };
     for (int i = 0; i < n; ++i)
-        if (a[i].ln.seg != kSeg && a[i].ln.seg != kSegAlt) return cudaErrorInvalidValue;
-    for (int seg : {kSeg, kSegAlt}) {
+        if (!seg_supported(a[i].ln.seg)) return cudaErrorInvalidValue;
+    for (int seg : {kSeg, kSegAlt, kSegLong}) {
         std::vector<int> order;
         for (int i = 0; i < n; ++i)
             if (a[i].ln.seg == seg) order.push_back(i);
         std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return len(i) > len(j); });
         const int m = (int)order.size();
         for (int k0 = 0; k0 < m; k0 += kBatch) {
-            cudaError_t e = seg == kSeg
-                                ? col_group_p<T, P, kBatch, kSeg>(a, maps, order.data() + k0, std::min(kBatch, m - k0), s)
-                                : col_group_p<T, P, kBatch, kSegAlt>(a, maps, order.data() + k0,
-                                                                     std::min(kBatch, m - k0), s);
+            const int nk = std::min(kBatch, m - k0);
+            cudaError_t e = seg == kSeg      ? col_group_p<T, P, kBatch, kSeg>(a, maps, order.data() + k0, nk, s)
+                            : seg == kSegAlt ? col_group_p<T, P, kBatch, kSegAlt>(a, maps, order.data() + k0, nk, s)
+                                             : col_group_p<T, P, kBatch, kSegLong>(a, maps, order.data() + k0, nk, s);
             if (e != cudaSuccess) return e;
         }
     }
@@ -1056,11 +1055,11 @@ cudaError_t col_group_dispatch(const ColArgs<T> *a, const ColMaps *maps, int n, 
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_rhs_group(int p, const RhsArgs<T> *a, int n, cudaStream_t s)
+template <typename T, int SEG>
+cudaError_t launch_rhs_seg(int p, const RhsArgs<T> *a, int n, cudaStream_t s)
 {
     if (!a || n <= 0) return cudaErrorInvalidValue;
-#define C(P) rhs_group_dispatch<T, P>(a, n, s)
+#define C(P) rhs_seg_p<T, P, SEG>(a, n, s)
     ADS_DISPATCH_P(p, C)
 #undef C
 }

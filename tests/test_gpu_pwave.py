@@ -89,6 +89,23 @@ def test_33_row_segments(ne, p, precision):
                 "%s %s p=%d" % (precision, ne, p))
 
 
+@pytest.mark.parametrize("tile", [None, "16"])
+@pytest.mark.parametrize("ne,p", [((128, 129, 4), 3), ((130, 129, 3), 2)])
+def test_44_row_segments(ne, p, tile, monkeypatch):
+    """FP32 planes of 129..132 unknowns per axis take 44-row segments (3 per
+    line, so that every line group of K1 runs in one round), the FP64 set-up
+    sweeps of the same simulation too; the whole-plane K1 and the row-tiled
+    K1 with the separate y sweep (K2) are covered."""
+    if tile:
+        monkeypatch.setenv("ADS_RHS_TILE", tile)
+    else:
+        monkeypatch.delenv("ADS_RHS_TILE", raising=False)
+    case = wl.ricker_case(ne=ne, p=p, tau=2e-3, steps=8, seed=11, sigma=0.05)
+    ref = oracle_wave(case, 8)
+    _, got = gpu_wave(case, 8, "fp32")
+    check_state(got[8], ref[8], "fp32", case.tau, TOL["fp32"], "%s p=%d tile %s" % (ne, p, tile))
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_fused_and_tiled_rhs_agree(precision, monkeypatch):
     """The fused K1 (tile = whole y extent, y sweep inside) and the tiled K1 +
