@@ -239,6 +239,11 @@ struct Vec2<float> { using type = float2; };
 template <>
 struct Vec2<double> { using type = double2; };
 
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // c + a * b on a pair of columns: one packed FP32 FMA (FFMA2) for float
 __device__ __forceinline__ float2 fma2(float a, float2 b, float2 c) { return __ffma2_rn(make_float2(a, a), b, c); }
 __device__ __forceinline__ double2 fma2(double a, double2 b, double2 c)
@@ -248,8 +253,12 @@ __device__ __forceinline__ double2 fma2(double a, double2 b, double2 c)
 
 constexpr int kPhase1Lookahead = 1;   // stream rows whose loads are in flight ahead of the one contracted
 
-template <typename T, int P, bool GUARD, bool INTERIOR, int PF = kPhase1Lookahead>
-__device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int sx, int my, const bool (&zok)[2 * P + 1],
+// Rows and planes outside the grid need no predicates: the band rows of M
+// and K hold zeros outside the matrix, so the loads read a clamped (valid)
+// row or plane and the zero coefficient drops its value.  zoff[k]: element
+// offset of plane clamp(z-P+k) (uniform over the CTA).
+template <typename T, int P, bool INTERIOR, int PF = kPhase1Lookahead>
+__device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zoff)[2 * P + 1], int sx, int my,
                                              const T (&cm)[2 * P + 1], const T (&ck)[2 * P + 1],
                                              const T (&mym)[2 * P + 1], const T (&myk)[2 * P + 1], const T *bMy,
                                              const T *bKy, int ylo, int yhi, int yb, int ye, T *s1col, T *s2col, int RS)
@@ -260,17 +269,13 @@ __device__ __forceinline__ void phase1_chunk(const T *col0, long long plane, int
 #pragma unroll
     for (int k = 0; k < W; ++k) r1[k] = r2[k] = V2{T(0), T(0)};
     const int n = ye - yb + 2 * P;
-    const T *rowp = col0 + (long long)(yb - P) * sx;
-    // the W plane values of stream row r (zero outside the grid or past the chunk)
+    // the W plane values of stream row r (row clamped into the grid: rows
+    // outside it, and those past the chunk, meet zero band entries or none)
     auto load_row = [&](int r, V2(&dst)[W]) {
-        const int yp = yb - P + r;
-        const bool ok = GUARD ? ((r < n) && yp >= 0 && yp < my) : (r < n);
-        const T *c = rowp + (long long)r * sx;
+        const int yp = min(max(yb - P + r, 0), my - 1);
+        const T *c = colx + (long long)yp * sx;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            const bool okk = GUARD ? (ok && zok[k]) : ok;
-            dst[k] = okk ? *reinterpret_cast<const V2 *>(c + (long long)k * plane) : V2{T(0), T(0)};
-        }
+        for (int k = 0; k < W; ++k) dst[k] = *reinterpret_cast<const V2 *>(c + zoff[k]);
     };
     // rows r .. r+PF-1 in flight: row r+PF's loads are issued before row r is contracted
     V2 pf[PF][W];
@@ -488,14 +493,34 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
         fence_mbar_init();
         mbar_expect_tx(&bar, (uint32_t)a.img_bytes);
         bulk_load(tb, a.img, (uint32_t)a.img_bytes, &bar);
+    }
+    if (!a.direct && warp == nwarps - 1) {
+        // the y band rows outside the Toeplitz range [lo, hi) are read from
+        // global memory by the boundary row chunks of phase 1: bring their
+        // cache lines into L1 now, so those reads do not wait on L2/DRAM
+        constexpr int LINE = 128 / sizeof(T);
+        const int lo = a.bandM[1].lo, hi = a.bandM[1].hi;
+        const int h = (lo < hi ? lo : my) * W, t0 = (lo < hi ? hi : my) * W, t1 = my * W;
+        const int nh = (h + LINE - 1) / LINE, nt = (t1 - t0 + LINE - 1) / LINE;
+        for (int i = lane; i < 2 * (nh + nt); i += 32) {
+            const T *band = (i & 1) ? a.bandK[1].v : a.bandM[1].v;
+            const int l = i >> 1;
+            prefetch_l1(band + (l < nh ? l * LINE : t0 + (l - nh) * LINE));
+        }
+    }
+    __syncthreads();   // barrier initialised
+    // the wavelet value r(t) (a step-counter load and FP64 arithmetic) is
+    // first read in phase 2, after the barrier that ends phase 1: one thread
+    // of a middle row chunk (whose phase-1 item has no boundary work)
+    // computes it while the others start
+    if (tid == NT / 2) {
         T r = T(0);
-        if (has_src) {   // overlaps the copy
+        if (has_src) {
             double t = (double)(a.step[0] + a.toff) * a.tau;
             r = (T)(a.src.amp * ricker_dev(a.src.freq, a.src.t0, t));
         }
         s_r = r;
     }
-    __syncthreads();   // barrier initialised, s_r set
 
     if (a.direct) {
         // ---- phase 1 (direct mode): the RHS is given; stage its rows into S1
@@ -510,15 +535,15 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
         const T *gMy = a.bandM[1].v, *gKy = a.bandK[1].v;
         T cm[W], ck[W], mym[W], myk[W];
         const int ylo = a.bandM[1].lo, yhi = a.bandM[1].hi;   // K shares M's interior range
-        bool zok[W];
+        long long zoff[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            cm[k] = a.bandM[2].v[z * W + k];
+            cm[k] = a.bandM[2].v[z * W + k];   // zero for planes outside the grid
             ck[k] = a.bandK[2].v[z * W + k];
             const int mid = ylo < yhi ? ylo : 0;
             mym[k] = gMy[mid * W + k];
             myk[k] = gKy[mid * W + k];
-            zok[k] = (z + k - P >= 0) && (z + k - P < mz);
+            zoff[k] = (long long)min(max(z + k - P, 0), mz - 1) * plane;
         }
         // work items (column pair, row chunk) spread over all lanes of the
         // CTA: as many chunks as keep every lane busy, whatever mx is
@@ -527,7 +552,6 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
         if (YC < 1) YC = 1;
         if (YC > tye) YC = tye;
         const int rows_per = (tye + YC - 1) / YC;
-        const bool zin = z >= P && z + P < mz;
         for (int item = tid; item < npair * YC; item += NT) {
             const int pr = item % npair, yc = item / npair;
             const int x = 2 * pr;
@@ -535,20 +559,15 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
             int ye = yb + rows_per;
             if (ye > y0 + tye) ye = y0 + tye;
             const bool live = yb < ye;
-            const bool guard = live && (!zin || yb - P < 0 || ye + P > my);
             const bool inter = !live || (yb >= ylo && ye <= yhi);
             // one variant per warp (lanes of two row chunks may share a warp)
-            const unsigned am = __activemask();
-            const bool wguard = __any_sync(am, guard), winter = __all_sync(am, inter);
+            const bool winter = __all_sync(__activemask(), inter);
             if (!live) continue;
-            const T *col0 = a.in + x + (long long)(z - P) * plane;   // plane z-P, row 0, column x
             T *c1 = S1 + x - (size_t)y0 * RS, *c2 = S2 + x - (size_t)y0 * RS;
-            if (!wguard && winter)
-                phase1_chunk<T, P, false, true>(col0, plane, sx, my, zok, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
-            else if (!wguard)
-                phase1_chunk<T, P, false, false>(col0, plane, sx, my, zok, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
+            if (winter)
+                phase1_chunk<T, P, true>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
             else
-                phase1_chunk<T, P, true, false>(col0, plane, sx, my, zok, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
+                phase1_chunk<T, P, false>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
         }
     }
     // tables in shared memory from here on; every thread leaves together if
