@@ -277,6 +277,15 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
  * ads_step(sim, 1).  Waits. */
 int ads_profile_step(ads_sim_t *sim, const char **names, float *ms, int cap, int *count);
 
+/* Measurement of the fused RHS kernel alone (Sec. 5.1: RHS by sum
+ * factorisation, x and y sweeps of eq. (25)): `reps` back-to-back launches
+ * on the simulation's stream, input the displacement-like state p, output
+ * the work field (overwritten; the state is not changed), bracketed by one
+ * pair of CUDA events after a 2 ms device-side sleep.  *ms_per_launch: the
+ * average device time per launch.  Scalar-wave simulations only
+ * (ADS_ERR_UNSUPPORTED otherwise); reps in [1, 10000].  Waits. */
+int ads_profile_rhs(ads_sim_t *sim, int reps, float *ms_per_launch);
+
 /* Kernel launches issued by this library since load (all simulations). */
 long long ads_launch_count(void);
 

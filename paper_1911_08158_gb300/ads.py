@@ -105,6 +105,7 @@ def library() -> ctypes.CDLL:
         L.ads_launch_count.restype = ctypes.c_longlong
         L.ads_profile_step.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), i,
                                        ctypes.POINTER(ctypes.c_int)]
+        L.ads_profile_rhs.argtypes = [vp, i, ctypes.POINTER(ctypes.c_float)]
         L.ads_last_error.restype = ctypes.c_char_p
         _lib = L
         return L
@@ -347,6 +348,13 @@ class Simulation:
         n = ctypes.c_int()
         _check(library().ads_profile_step(self._h, names, ms, 8, ctypes.byref(n)))
         return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, 8))]
+
+    def profile_rhs(self, reps: int = 20) -> float:
+        """Average device time (ms) of the fused RHS kernel over `reps`
+        back-to-back launches (ads_profile_rhs); the state is not changed."""
+        ms = ctypes.c_float()
+        _check(library().ads_profile_rhs(self._h, int(reps), ctypes.byref(ms)))
+        return float(ms.value)
 
     @property
     def device_bytes(self) -> int:

@@ -2055,4 +2055,39 @@ int ads_profile_step(ads_sim_t *s, const char **names, float *ms, int cap, int *
     return ADS_OK;
 }
 
+int ads_profile_rhs(ads_sim_t *s, int reps, float *ms_per_launch)
+{
+    if (!s || !ms_per_launch || reps < 1 || reps > 10000)
+        return fail(ADS_ERR_INVALID_ARG, "ads_profile_rhs: bad arguments");
+    if (s->kind != ADS_SCALAR_WAVE) return fail(ADS_ERR_UNSUPPORTED, "ads_profile_rhs: scalar-wave simulations only");
+    cudaSetDevice(s->device);
+    cudaEvent_t e[2];
+    ADS_CK(cudaEventCreate(&e[0]));
+    if (cudaEventCreate(&e[1]) != cudaSuccess) {
+        cudaEventDestroy(e[0]);
+        return fail(ADS_ERR_CUDA, "ads_profile_rhs: cudaEventCreate failed");
+    }
+    // the K1 launch of a step, repeated: it reads p and overwrites the work field only
+    auto run = [&]() -> int {
+        ADS_CK(ads::launch_delay(2000000ull, s->stream));
+        ADS_CK(cudaEventRecord(e[0], s->stream));
+        for (int i = 0; i < reps; ++i) {
+            if (s->prec == ADS_FP64)
+                ADS_CK(ads::launch_rhs<double>(s->p, s->seg, pwave_launch<double>(s, false).rhs, s->stream));
+            else
+                ADS_CK(ads::launch_rhs<float>(s->p, s->seg, pwave_launch<float>(s, false).rhs, s->stream));
+        }
+        ADS_CK(cudaEventRecord(e[1], s->stream));
+        ADS_CK(cudaEventSynchronize(e[1]));
+        float t = 0.f;
+        ADS_CK(cudaEventElapsedTime(&t, e[0], e[1]));
+        *ms_per_launch = t / reps;
+        return ADS_OK;
+    };
+    const int rc = run();
+    cudaEventDestroy(e[0]);
+    cudaEventDestroy(e[1]);
+    return rc;
+}
+
 }  // extern "C"

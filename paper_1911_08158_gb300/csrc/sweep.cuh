@@ -509,6 +509,9 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
         }
     }
     __syncthreads();   // barrier initialised
+    // everything above reads static tables only; p, the step counter and the
+    // output buffer belong to the previous kernels of the stream
+    griddep_wait();
     // the wavelet value r(t) (a step-counter load and FP64 arithmetic) is
     // first read in phase 2, after the barrier that ends phase 1: one thread
     // of a middle row chunk (whose phase-1 item has no boundary work)
@@ -766,7 +769,11 @@ __global__ void __launch_bounds__(512) k_col(const __grid_constant__ ColGroup<T,
         if (staged) mbar_init(&bar, 1);
         fence_mbar_init();
         mbar_expect_tx(&bar_tab, (uint32_t)a.ln.bytes);
-        bulk_load(lb, a.ln.base, (uint32_t)a.ln.bytes, &bar_tab);
+        bulk_load(lb, a.ln.base, (uint32_t)a.ln.bytes, &bar_tab);   // static line tables
+    }
+    // the input line, p, q and the step counter belong to the previous kernels of the stream
+    griddep_wait();
+    if (tid == 0) {
         if (upd && blk == 0) a.step[0] += 1;
         if (staged) {
             mbar_expect_tx(&bar, 2u * nch * 32u * box * sizeof(T));
@@ -901,25 +908,27 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
         smem_set = smem;
     }
     ++g_launches;
-    if (!PAIR) {
-        k_rhs<T, P, NB, SEG, LAYOUT><<<(unsigned)blocks, RhsThreads<T, LAYOUT>::value, smem, s>>>(g);
-        return cudaGetLastError();
-    }
-    // two CTAs per cluster: the halves of one z-plane (every simulation's
-    // block range has an even length, so clusters never straddle two)
+    // programmatic dependent launch: the kernel's prologue overlaps the tail
+    // of the previous kernel of the stream (it waits for that kernel before
+    // touching its data); pairs: two CTAs per cluster, the halves of one
+    // z-plane (every simulation's block range has an even length, so
+    // clusters never straddle two)
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)blocks, 1, 1);
     cfg.blockDim = dim3(RhsThreads<T, LAYOUT>::value, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute attr[2];
+    std::memset(attr, 0, sizeof(attr));
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = 2;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = PAIR ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, k_rhs<T, P, NB, SEG, LAYOUT>, g);
 }
 
@@ -1035,9 +1044,21 @@ cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *ord
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    k_col<T, P, NB, SEG><<<(unsigned)blocks, 32 * smax, smem, s>>>(g);
+    // programmatic dependent launch (the kernel waits for the previous one before reading its data)
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+    cfg.blockDim = dim3(32 * smax, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    std::memset(attr, 0, sizeof(attr));
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     ++g_launches;
-    return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_col<T, P, NB, SEG>, g);
 }
 
 template <typename T, int P>

@@ -96,4 +96,12 @@ __device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk
 // wait until the shared-memory sources of all committed stores have been read
 __device__ __forceinline__ void tma_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched with the
+// programmatic-stream-serialization attribute may be scheduled as the CTAs
+// of the previous kernel of the stream exit (no early trigger: measured, an
+// early one let the next grid's waiting CTAs take SMs and slowed the step).
+// Wait until the previous grid has completed and its writes are visible (a
+// no-op when the launch had no such dependency).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace ads

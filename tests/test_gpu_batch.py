@@ -171,6 +171,27 @@ def test_autotune_keeps_state_and_picks_a_candidate():
     assert t.autotune(2) == rows
 
 
+def test_profile_rhs_keeps_state():
+    """ads_profile_rhs times repeated launches of the fused RHS kernel: a
+    positive time per launch, no change of the state or the step counter."""
+    from paper_1911_08158_gb300 import AdsError
+    c = wl.ricker_case(ne=(24, 20, 18), p=3, tau=2e-3, steps=0, seed=2, sigma=0.05)
+    s = _make(c, "fp32")
+    s.step(4)
+    before = s.get_state()
+    ms = s.profile_rhs(5)
+    assert 0 < ms < 100
+    after = s.get_state()
+    assert s.step_count == 4
+    for k in range(3):
+        assert np.array_equal(before[k], after[k])
+    s.step(4)
+    ref = oracle_wave(c, 8)[8]
+    check_state(s.get_state(), ref, "fp32", c.tau, 1e-5, "after ads_profile_rhs")
+    with pytest.raises(AdsError):
+        s.profile_rhs(0)
+
+
 def test_batch_rejects_bad_arguments():
     from paper_1911_08158_gb300 import AdsError, batch_step
     s = _make(wl.pulse_case(ne=6, p=2, steps=0), "fp32")
