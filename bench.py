@@ -165,7 +165,9 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     sims = make_sims("fp32", torch, ads, wl, stream)
-    tiles = [s.autotune(3) for s in sims]
+    # 0 trial steps: the first candidate (the fused single-CTA K1 when it
+    # fits), a choice that does not depend on timings (for profiler runs)
+    tiles = [s.autotune(args.autotune_steps) for s in sims]
     dof_steps = sum(dofs(s) for s in sims) * NSTEPS
 
     def bench_step():
@@ -544,6 +546,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-elastic", action="store_true", help="skip the elasticity measurement")
     ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--autotune-steps", type=int, default=3,
+                    help="trial steps per K1 layout candidate (0: take the first candidate)")
     ap.add_argument("--profile-case", default="", help="run a small case (n or nx,ny,nz elements) for ncu and exit")
     ap.add_argument("--profile-p", type=int, default=2)
     ap.add_argument("--profile-batch", type=int, default=1, help="simulations advanced together in the profile case")
