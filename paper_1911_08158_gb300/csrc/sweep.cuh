@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -281,10 +282,17 @@ __device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zo
     V2 pf[PF][W];
 #pragma unroll
     for (int d = 0; d < PF; ++d) load_row(d, pf[d]);
-    for (int r0 = 0; r0 < n; r0 += W) {
+    // one block of W stream rows (ring slots static after unrolling); TAIL:
+    // the last, partial block stops at the stream end (a check that full
+    // blocks do without: it would keep the next row's loads from being
+    // hoisted)
+    auto block = [&](int r0, auto tail) {
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             const int r = r0 + j;
+            if constexpr (decltype(tail)::value) {
+                if (r >= n) break;
+            }
             V2 nv[W];
             load_row(r + PF, nv);
             const V2(&v)[W] = pf[0];
@@ -327,7 +335,10 @@ __device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zo
 #pragma unroll
             for (int k = 0; k < W; ++k) pf[PF - 1][k] = nv[k];
         }
-    }
+    };
+    int r0 = 0;
+    for (; r0 + W <= n; r0 += W) block(r0, std::false_type{});
+    if (r0 < n) block(r0, std::true_type{});
 }
 
 // Phase 2 of K1, pass 1 for one row segment [b0, b0+n): form
