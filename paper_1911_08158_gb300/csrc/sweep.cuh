@@ -230,9 +230,9 @@ __device__ __forceinline__ void band_row(const T *tab, int lo, int hi, const T (
 // stream the rows yp = yb-P .. ye+P-1, z-contract each (t1 = Mz p,
 // t2 = Kz p) into a ring of W slots, and y-contract every complete window
 // into s1, s2.  The loop is unrolled by W so that ring slots are static
-// registers.  GUARD: rows or planes may fall outside the grid (zero);
-// INTERIOR: every output row lies in the Toeplitz range (band rows from
-// registers).  Column x+1 may be the zero padding of the row (x+1 = mx).
+// registers.  Rows and planes outside the grid are read clamped and meet
+// zero band entries (see phase1_chunk).  Column x+1 may be the zero padding
+// of the row (x+1 = mx).
 template <typename T>
 struct Vec2;
 template <>
