@@ -48,6 +48,11 @@ def test_invalid_arguments_rejected_on_host():
     with pytest.raises(ads.AdsError) as e:
         ads.Simulation((4, 0, 4), 2, 0.01, use_torch=False)
     assert e.value.code == -1
+    # measurement calls validate their arguments before touching the device
+    L = ads.library()
+    ms = ctypes.c_float()
+    assert L.ads_profile_rhs(None, 5, ctypes.byref(ms)) == -1
+    assert L.ads_profile_rhs(None, 5, None) == -1
 
 
 def test_estimate_bytes_is_host_only_and_consistent():
