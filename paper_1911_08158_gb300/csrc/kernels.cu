@@ -17,6 +17,12 @@ namespace ads {
 
 std::atomic<unsigned long long> g_launches{0};
 
+std::mutex &attr_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+
 namespace {
 
 // ---------------------------------------------------------------- helpers
@@ -587,12 +593,9 @@ cudaError_t launch_axis_apply(int p, const T *band, int axis, const T *in, T *ou
 template <typename T, int P>
 cudaError_t kron_sum_impl(dim3 grid, size_t smem, cudaStream_t s, const KronSum<T> &ks, T *out, Dims d, int ty)
 {
-    static size_t smem_set = 48 * 1024;   // per instantiation: opt-in dynamic shared memory (set outside capture)
-    if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_kron_sum<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-    }
+    static std::atomic<size_t> smem_set{48 * 1024};   // per instantiation (raised outside capture)
+    cudaError_t e = raise_dyn_smem(k_kron_sum<T, P>, smem_set, smem);
+    if (e != cudaSuccess) return e;
     k_kron_sum<T, P><<<grid, 256, smem, s>>>(ks, out, d, ty);
     return cudaGetLastError();
 }

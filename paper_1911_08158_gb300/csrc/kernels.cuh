@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 
 namespace ads {
 
@@ -255,5 +256,21 @@ cudaError_t launch_wait_selftest(long long cycles, int *err, cudaStream_t s);
 
 // kernel launches issued by the library (all host threads)
 extern std::atomic<unsigned long long> g_launches;
+
+// Opt-in dynamic shared memory of one kernel, raised to at least `smem`
+// bytes.  `cur` (one per kernel instantiation) only grows, under one lock,
+// and only after the attribute holds it, so host threads that launch the
+// same kernel with different sizes never lower it under one another.
+std::mutex &attr_mutex();
+template <typename K>
+cudaError_t raise_dyn_smem(K *kernel, std::atomic<size_t> &cur, size_t smem)
+{
+    if (smem <= cur.load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(attr_mutex());
+    if (smem <= cur.load(std::memory_order_relaxed)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cur.store(smem, std::memory_order_release);
+    return e;
+}
 
 }  // namespace ads

@@ -911,13 +911,8 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
     if (blocks <= 0 || blocks > (1ll << 30)) return cudaErrorInvalidValue;
     g.off[n] = (int)blocks;
     g.n = n;
-    static size_t smem_set = 48 * 1024;   // per instantiation: opt-in dynamic shared memory
-    if (smem > smem_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_rhs<T, P, NB, SEG, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-    }
+    static std::atomic<size_t> smem_set{48 * 1024};   // per instantiation: opt-in dynamic shared memory
+    if (cudaError_t e = raise_dyn_smem(k_rhs<T, P, NB, SEG, LAYOUT>, smem_set, smem); e != cudaSuccess) return e;
     ++g_launches;
     // programmatic dependent launch: the kernel's prologue overlaps the tail
     // of the previous kernel of the stream (it waits for that kernel before
@@ -1049,12 +1044,8 @@ cudaError_t col_group_p(const ColArgs<T> *a, const ColMaps *maps, const int *ord
     if (blocks <= 0 || blocks > (1ll << 30)) return cudaErrorInvalidValue;
     g.off[n] = (int)blocks;
     g.n = n;
-    static size_t smem_set = 48 * 1024;
-    if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_col<T, P, NB, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-    }
+    static std::atomic<size_t> smem_set{48 * 1024};
+    if (cudaError_t e = raise_dyn_smem(k_col<T, P, NB, SEG>, smem_set, smem); e != cudaSuccess) return e;
     // programmatic dependent launch (the kernel waits for the previous one before reading its data)
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
