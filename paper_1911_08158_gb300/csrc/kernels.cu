@@ -521,8 +521,12 @@ int choose_seg(const int *m, int elem)
         if (Sx > 16 || Sy > 16) return 1 << 30;
         return seg * (line_rounds(m[1], Sx, warps) + line_rounds(m[0], Sy, warps));
     };
-    const int Sz = (m[2] + kSegLong - 1) / kSegLong;
-    if (Sz <= 16 && cost(kSegLong) < cost(best)) best = kSegLong;
+    // 44-row lines take at most 8 segments: K1 at 44 rows exists in the
+    // single-CTA layout only, whose FP64 CTA (the set-up and residual sweeps
+    // of every simulation) has 8 warps
+    const int S44[3] = {(m[0] + kSegLong - 1) / kSegLong, (m[1] + kSegLong - 1) / kSegLong,
+                        (m[2] + kSegLong - 1) / kSegLong};
+    if (S44[0] <= 8 && S44[1] <= 8 && S44[2] <= 16 && cost(kSegLong) < cost(best)) best = kSegLong;
     return best;
 }
 
