@@ -72,7 +72,10 @@ def test_zero_steps_and_empty_batch():
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_elasticity_long_lines(precision):
-    """Diagonal-block sweeps of more than 8 segments (wide FP64 CTA)."""
+    """Long diagonal-block sweeps: 300 unknowns along x (FP32: 10 segments of
+    32 rows; FP64: 7 segments of 44 rows in the 256-thread CTA).  The wide
+    FP64 CTA (more than 8 segments) is covered by the 510- and 512-unknown
+    lines of test_longest_lines and test_2d_long_lines_fp64."""
     from tests.cases import assert_parity, gpu_elastic, oracle_elastic
     case = wl.elastic_case(ne=(300, 4, 3), p=2, tau=4e-3, steps=6, seed=5, sigma=0.1)
     ref = oracle_elastic(case, 6)[6]
@@ -93,6 +96,8 @@ def test_2d_long_lines_fp64(boundary):
 
 
 def test_batch_mixing_wide_and_narrow_fp64():
+    """One batch of two FP64 simulations with different K1 instantiations
+    (300 unknowns along x: 44-row segments; the small one: 32-row segments)."""
     from paper_1911_08158_gb300 import Simulation, batch_step
     cases = [wl.ricker_case(ne=(300, 3, 2), p=2, tau=2e-3, steps=0, seed=1, sigma=0.05),
              wl.ricker_case(ne=(10, 9, 8), p=2, tau=2e-3, steps=0, seed=2, sigma=0.05)]
