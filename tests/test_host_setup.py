@@ -92,3 +92,41 @@ def test_partitioned_solve_equals_plain_substitution(checker, ne, p, natural, se
     r = _run(checker, ne, p, natural, 1e-5, seg)
     assert r["segments"] == -(-m // seg)
     assert r["part_err"] <= 1e-13
+
+
+def _choose_seg():
+    """The library's segment-length rule (internal C++ symbol ads::choose_seg)."""
+    import ctypes
+    from paper_1911_08158_gb300 import library
+    f = getattr(library(), "_ZN3ads10choose_segEPKii")
+    f.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    f.restype = ctypes.c_int
+    return lambda m, elem: f((ctypes.c_int * 3)(*m), elem)
+
+
+@pytest.mark.parametrize("m,elem,seg", [
+    ((128, 128, 128), 4, 32),      # 4 line groups x 4 segments: one round of 16 warps
+    ((129, 129, 129), 4, 44),      # 5 groups: 3 segments of 44 rows fit one round, 4 of 33 do not
+    ((129, 129, 129), 8, 33),      # FP64 CTA of 8 warps: 44 rows save no round
+    ((97, 130, 5), 4, 33),         # 32 s + 1 unknowns: one segment fewer with 33 rows
+    ((130, 129, 3), 4, 44),
+    ((176, 176, 176), 4, 44),      # 6 groups: 4 segments of 44 (2 rounds) vs 6 of 32 (3 rounds)
+    ((70, 70, 70), 8, 44),         # FP64: 2 segments of 44 (one round) vs 3 of 32 (two)
+    ((300, 4, 3), 8, 44),          # 7 segments of 44 rows: the 256-thread FP64 CTA
+    ((400, 300, 10), 8, 32),       # more than 8 segments of 44: K1 has no wide 44-row CTA
+    ((265, 360, 10), 4, 33),       # 9 segments of 44 along y: excluded; 33 rows save a segment over 32
+    ((512, 4, 4), 4, 32),
+])
+def test_segment_length_choice(m, elem, seg):
+    assert _choose_seg()(m, elem) == seg
+
+
+def test_segment_length_never_exceeds_what_k1_instantiates():
+    """44-row segments only while every line takes at most 8 of them (the
+    single-CTA layout, also in FP64), for all axis lengths up to 512."""
+    choose = _choose_seg()
+    for a in range(1, 513, 3):
+        for b in range(1, 513, 5):
+            for elem in (4, 8):
+                if choose((a, b, 17), elem) == 44:
+                    assert -(-a // 44) <= 8 and -(-b // 44) <= 8, (a, b, elem)
