@@ -164,3 +164,45 @@ def test_second_order_in_time_general_data():
         errs.append(np.linalg.norm(u - ref_u))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(rates - 2.0) < 0.15), rates
+
+
+def _interior_basis_at_gauss(ne, p, q):
+    """Gauss points and weights on [0, 1] (q per element) and the values of the
+    Dirichlet-restricted basis there (rows: points, columns: interior functions)."""
+    gx, gw = np.polynomial.legendre.leggauss(q)
+    X, Wq, B = [], [], []
+    for e in range(ne):
+        a, h = e / ne, 1.0 / ne
+        for xg, wg in zip(gx, gw):
+            x = a + 0.5 * h * (xg + 1)
+            N, _ = ora.basis(ne, p, p + e, x)
+            X.append(x)
+            Wq.append(0.5 * h * wg)
+            B.append(N[1:-1])
+    return np.array(X), np.array(Wq), np.array(B)
+
+
+@pytest.mark.parametrize("p,nes,T,N", [(1, (6, 12, 24), 0.3, 1600), (2, (6, 12, 24), 0.3, 1600),
+                                       (3, (4, 8, 16), 0.1, 4000)])
+def test_standing_wave_converges_in_space_at_order_p_plus_1(p, nes, T, N):
+    """Spatial order of the whole scheme (soft pin; the paper states no rate):
+    u = sin(pi x) sin(pi y) sin(pi z) cos(sqrt(3) pi t) solves u_tt = Laplace u
+    with homogeneous Dirichlet data.  L2-project u(0), step with a time step
+    small enough that the O(tau^2) error stays well below the spatial one, and
+    measure the L2 error at T by tensor Gauss quadrature: it falls as h^(p+1)
+    (measured log2 ratios: p=1 2.00 2.00, p=2 3.40 3.15, p=3 4.24 4.09)."""
+    errs = []
+    for ne in nes:
+        s = ora.Space((ne, ne, ne), p)
+        X, Wq, B = _interior_basis_at_gauss(ne, p, p + 3)
+        f = np.sin(np.pi * X)
+        c = np.linalg.solve(s.mat(0, "M"), B.T @ (Wq * f))       # 1D projection of sin(pi x)
+        U0 = np.einsum("k,j,i->kji", c, c, c)                       # the 3D projection is its product
+        u, _, _ = s.pwave_run(U0, np.zeros_like(U0), s.pwave_accel(U0), T / N, N)
+        uh = np.einsum("kbc,ak->abc", np.einsum("kjc,bj->kbc", u @ B.T, B), B)
+        exact = np.einsum("a,b,c->abc", f, f, f) * np.cos(np.sqrt(3) * np.pi * T)
+        w3 = np.einsum("a,b,c->abc", Wq, Wq, Wq)
+        errs.append(np.sqrt(np.sum(w3 * (uh - exact) ** 2)))
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert abs(rates[-1] - (p + 1)) < 0.2, (errs, rates)
+    assert all(p + 1 - 0.2 < r < p + 1 + 0.5 for r in rates), (errs, rates)
