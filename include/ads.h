@@ -174,19 +174,42 @@ int ads_set_source_field(ads_sim_t *sim, const double *g, size_t count, int mem,
  * + tau^2/2 A0, A0 = (rho M)^{-1}(f^0 - Ups U0). */
 int ads_set_gaussian_state(ads_sim_t *sim, const ads_gaussian_t *u0, const ads_gaussian_t *v0);
 
-/* Set the state from coefficient arrays (count = comps*n0*n1*n2 each).
- * Scalar wave: u, v required; a may be NULL (then a = M^{-1}(F(t_n) - K u)).
+/* Set the state from coefficient arrays (count = comps*n0*n1*n2 each): the
+ * B-spline coefficients of the discrete fields of Sec. 2 (u = sum_abc
+ * N_a N_b N_c U_abc; the Newmark state u_n, v_n, a_n of eq. pwave2) or of
+ * Sec. 5 (the three-level state U^n, U^{n-1} of eq. gen).
+ * Scalar wave: u, v required; a may be NULL (then a = M^{-1}(F(t_n) - K u),
+ * the consistent acceleration of the first line of eq. scheme at t_n).
  * Elasticity: u = U^n, v = V^n; a must be NULL; U^{n-1} as in
- * ads_set_gaussian_state.  The step counter is left unchanged. */
+ * ads_set_gaussian_state.  The step counter is left unchanged.  The FP32
+ * path rounds the state to FP32 here.  Errors: INVALID_ARG (null sim, u or
+ * v, wrong count, a given for elasticity, unknown mem), OOM (staging
+ * memory), CUDA. */
 int ads_set_state(ads_sim_t *sim, const double *u, const double *v, const double *a, size_t count,
                   int mem);
 
-/* Read the state; any output may be NULL.  Scalar wave: u_n, v_n, a_n.
- * Elasticity: u = U^n, v = (U^n - U^{n-1})/tau; a must be NULL.
- * Waits for the stream. */
+/* Read the state (B-spline coefficient arrays, layout as ads_set_state);
+ * any output may be NULL.  Scalar wave: u_n, v_n, a_n of the Newmark update
+ * of eq. pwave2 (u_n = p - q + eta a_n, tau v_n = q - tau^2/2 a_n from the
+ * two device arrays p = u + tau v + eta a, q = tau v + tau^2/2 a).
+ * Elasticity: u = U^n, v = (U^n - U^{n-1})/tau (the difference quotient of
+ * the three-level scheme, eq. gen); a must be NULL.  Waits for the stream;
+ * reports a device-side error (ADS_ERR_TIMEOUT for an expired bounded wait)
+ * recorded by earlier steps. */
 int ads_get_state(ads_sim_t *sim, double *u, double *v, double *a, size_t count, int mem);
 
-/* Advance nsteps >= 0 time steps (asynchronous on the stream). */
+/* Advance nsteps >= 0 time steps (asynchronous on the stream).
+ * Scalar wave, one step (Sec. 2, eq. pwave2, read as average-acceleration
+ * Newmark with the split operator):
+ *   R = F_{n+1} - K (u_n + tau v_n + eta a_n), K by sum factorisation of the
+ *   Gauss-quadrature integrals (Sec. 2, eqs. for M_x, K_x);
+ *   a_{n+1} = (Ax (x) Ay (x) Az)^{-1} R by three directional banded solves
+ *   over every grid line (Appendix);  u, v updated as in eq. pwave2.
+ * Elasticity, one step of the alternating-triangular scheme (Sec. 5, eqs.
+ *   decom, pre, corr, spill, gen with sigma = 1/2): block-lower sweep,
+ *   rho M, block-upper sweep, U^{n+1} = 2U^n - U^{n-1} + delta.
+ * Runs of 16 steps replay a captured CUDA graph.  Errors: INVALID_ARG,
+ * CUDA; device-side errors surface at the next waiting call. */
 int ads_step(ads_sim_t *sim, int nsteps);
 
 /* Advance `count` distinct simulations (same device) by nsteps each.
@@ -235,22 +258,28 @@ int ads_energy(ads_sim_t *sim, double *kinetic, double *potential, double *kin_m
  * scalar field (count = n0*n1*n2 doubles), in FP64 on the device.  Waits. */
 int ads_apply(ads_sim_t *sim, int op, const double *in, double *out, size_t count, int mem);
 
-/* ads_apply for callers that must not allocate device memory while they
- * run (for example code issuing work while a stream is being captured into
- * a CUDA graph, or a loop whose memory is fixed up front).  The paper has no
- * counterpart: this is a property of the library, not of the method.
- *   in, out: DEVICE pointers to FP64 fields of the full space (count =
- *            n0*n1*n2, boundary coefficients ignored / written as zero).
+/* ads_apply for callers that cannot allocate device memory during the call:
+ * a host application whose device memory is handed out in full up front (a
+ * pool owned by another framework, a fixed per-process budget), or a loop
+ * that cannot take the synchronisation and latency cudaMalloc and cudaFree
+ * may cost.  ads_apply allocates two scratch fields per call; this variant
+ * calls no cudaMalloc, cudaFree or allocating library routine.  The paper
+ * has no counterpart: this is a property of the library, not of the method.
+ *   in, out: DEVICE pointers on the simulation's device to FP64 fields of
+ *            the full space (count = n0*n1*n2, boundary coefficients ignored
+ *            / written as zero); other memory is rejected with
+ *            ADS_ERR_INVALID_ARG.
  *   Scratch: a fixed array compiled into the library, two fields of at most
  *            524288 doubles each (8 MiB, held by every GPU that loads the
  *            library until the process exits); spaces whose padded interior
- *            is larger are rejected with ADS_ERR_UNSUPPORTED.  No cudaMalloc,
- *            cudaFree or allocating library routine is called.
+ *            is larger are rejected with ADS_ERR_UNSUPPORTED.
  *   The first call on a device resolves the array's device address
  *   (cudaGetSymbolAddress); make that first call before any stream capture.
- *   All calls share the one array: calls whose work overlaps on the GPU (two
- *   streams, two simulations at once) race; serialise them.  Waits for the
- *   simulation's stream. */
+ *   All calls share the one array and each leaves its contents behind (a
+ *   call clears what it reads first): calls whose work overlaps on the GPU
+ *   (two streams, two simulations at once) race; serialise them.  The call
+ *   waits for the simulation's stream and then reads the simulation's
+ *   device error word (a blocking copy). */
 int ads_apply_noalloc(ads_sim_t *sim, int op, const double *in, double *out, size_t count);
 
 /* Checkpoint: the raw device state (all precisions bit-exact) plus the
@@ -277,14 +306,27 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
  * ads_step(sim, 1).  Waits. */
 int ads_profile_step(ads_sim_t *sim, const char **names, float *ms, int cap, int *count);
 
-/* Measurement of the fused RHS kernel alone (Sec. 5.1: RHS by sum
- * factorisation, x and y sweeps of eq. (25)): `reps` back-to-back launches
+/* Measurement of the fused RHS kernel alone (Sec. 2, eq. pwave2: the
+ * right-hand side F_{n+1} - K p by sum factorisation, then the x and y
+ * directional solves of the Appendix): `reps` back-to-back launches
  * on the simulation's stream, input the displacement-like state p, output
  * the work field (overwritten; the state is not changed), bracketed by one
  * pair of CUDA events after a 2 ms device-side sleep.  *ms_per_launch: the
  * average device time per launch.  Scalar-wave simulations only
  * (ADS_ERR_UNSUPPORTED otherwise); reps in [1, 10000].  Waits. */
 int ads_profile_rhs(ads_sim_t *sim, int reps, float *ms_per_launch);
+
+/* Measurement of the device's CUDA-core arithmetic peak (the paper has no
+ * counterpart; it gives the compute ceiling beside the HBM one for the
+ * line sweeps): one launch of 8 CTAs x 256 threads per SM, each thread
+ * running 8 independent FMA chains for `iters` rounds (1 .. 2^24), timed
+ * with CUDA events on a stream of its own after one warm-up launch.
+ * kind 0: FP64 DFMA; 1: FP32 FFMA; 2: packed FP32 FFMA2 (two FMAs per
+ * instruction).  *tflops = 2 x FMAs / device time (TFLOP/s); *ms (nullable)
+ * = the device time.  device < 0: the current device.  The clocks are
+ * whatever the device runs at: this call changes no setting.  Allocates 64
+ * bytes for the duration of the call.  Waits. */
+int ads_measure_fma_peak(int device, int kind, int iters, double *tflops, double *ms);
 
 /* Kernel launches issued by this library since load (all simulations). */
 long long ads_launch_count(void);
