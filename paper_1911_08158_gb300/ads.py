@@ -106,6 +106,7 @@ def library() -> ctypes.CDLL:
         L.ads_profile_step.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), i,
                                        ctypes.POINTER(ctypes.c_int)]
         L.ads_profile_rhs.argtypes = [vp, i, ctypes.POINTER(ctypes.c_float)]
+        L.ads_measure_fma_peak.argtypes = [i, i, i, _D, _D]
         L.ads_last_error.restype = ctypes.c_char_p
         _lib = L
         return L
@@ -208,6 +209,7 @@ class Simulation:
                             ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
         self.kind, self.p, self.tau, self.precision = kind, int(p), float(tau), precision
+        self.device = int(device)
         self.n_elem, self.length = ne, ln
         n = (ctypes.c_int * 3)()
         comps = ctypes.c_int()
@@ -320,13 +322,15 @@ class Simulation:
         return out
 
     def apply_noalloc(self, op: int, x, out):
-        """ads_apply_noalloc on CUDA float64 tensors of the full scalar space
-        (no device allocation inside the call)."""
+        """ads_apply_noalloc on CUDA float64 tensors of the full scalar space,
+        on the simulation's device (no device allocation inside the call)."""
         n1 = int(np.prod(self.n))
         px, mx_, _ = _ptr(x, n1)
         po, mo, _ = _ptr(out, n1)
         if mx_ != ADS_DEVICE or mo != ADS_DEVICE:
             raise ValueError("apply_noalloc takes CUDA tensors")
+        if x.device.index != self.device or out.device.index != self.device:
+            raise ValueError("apply_noalloc: tensors must live on the simulation's device cuda:%d" % self.device)
         _check(library().ads_apply_noalloc(self._h, int(op), px, po, n1))
 
     def checkpoint(self) -> bytes:
@@ -371,6 +375,16 @@ def selftest_timeout(device: int = 0, cycles: int = 20_000_000) -> int:
     """Run the bounded-wait self-test (ads_selftest_timeout); returns its code
     (ADS_ERR_TIMEOUT = -4 is the expected outcome)."""
     return int(library().ads_selftest_timeout(int(device), int(cycles)))
+
+
+def measure_fma_peak(kind: str = "ffma2", device: int = 0, iters: int = 1 << 16):
+    """CUDA-core FMA throughput of the device (ads_measure_fma_peak):
+    kind 'dfma' (FP64), 'ffma' (FP32) or 'ffma2' (packed FP32); returns
+    (TFLOP/s, device ms)."""
+    k = {"dfma": 0, "ffma": 1, "ffma2": 2}[kind]
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(library().ads_measure_fma_peak(int(device), k, int(iters), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def estimate_bytes(n_elem, p: int, kind: str = "wave", precision: str = "fp32", boundary: str = "dirichlet") -> int:

@@ -1999,7 +1999,7 @@ int ads_internal_apply_scratch(ads_sim_t *s, int op, const double *in, double *o
     if (count != nf) return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: count must be n0*n1*n2");
     if (op == ADS_OP_SPLIT_SOLVE && s->kind != ADS_SCALAR_WAVE)
         return fail(ADS_ERR_INVALID_ARG, "ads_apply_noalloc: split solve is defined for the scalar wave");
-    cudaSetDevice(s->device);
+    // (the caller has made the simulation's device current)
     // interior scratch starts from zero (padding columns are read as zeros)
     ADS_CK(cudaMemsetAsync(s0, 0, (size_t)s->d.count() * sizeof(double), s->stream));
     ADS_CK(cudaMemsetAsync(s1, 0, (size_t)s->d.count() * sizeof(double), s->stream));

@@ -10,7 +10,8 @@ size_t ads_internal_interior_count(const ads_sim_t *sim);
 
 // Apply ADS_OP_* like ads_apply to device arrays `in`/`out` (full space,
 // FP64), using the caller's two interior scratch fields s0, s1 (each at least
-// ads_internal_interior_count doubles) instead of allocating.  Waits.
+// ads_internal_interior_count doubles) instead of allocating.  The caller
+// makes the simulation's device current.  Waits.
 int ads_internal_apply_scratch(ads_sim_t *sim, int op, const double *in, double *out, size_t count, double *s0,
                                double *s1);
 
