@@ -50,13 +50,39 @@ UNIT = "DOF-steps/s"
 NE, NSTEPS, PS = 128, 200, (2, 3)
 WORKLOAD = "pwave_ricker_128cubed_p2p3_200steps"
 
-# algorithmic bytes per interior DOF of one launch (FP32), see the design doc
+# algorithmic bytes per interior DOF of one launch (FP32): one read or write
+# of each array element the kernel must touch
 ALG_BYTES = {
     "rhs_xy_sweep": 8,      # read p, write x-and-y-swept field
     "rhs_x_sweep": 8,       # read p, write x-swept field
     "y_sweep": 8,           # read, write
     "z_sweep_update": 24,   # read swept field, p, q; write p, q, a (a is written in profiled steps)
 }
+
+
+def step_flops(p: int) -> dict:
+    """Algorithmic FLOPs per interior unknown of one scalar-wave step (the
+    method's own arithmetic, without the partitioned solve's corrections):
+    RHS by sum factorisation 14(2p+1) + 3 (z: Mz, Kz; y: My, Ky, My; x: Kx,
+    Mx; source and scale), each directional banded solve 4p + 1 (p FMAs
+    forward, p back, one pivot multiply), the (p, q) update 3."""
+    w = 2 * p + 1
+    rhs, sweep, upd = 14 * w + 3, 4 * p + 1, 3
+    return {"rhs": rhs, "sweep": sweep, "update": upd, "k1_fused": rhs + 2 * sweep,
+            "step": rhs + 3 * sweep + upd}
+
+
+def measure_peaks(ads, local):
+    """FMA throughput of the device's CUDA cores (ads_measure_fma_peak), with
+    the clocks sampled while it runs."""
+    out = {}
+    with ClockSampler(local) as clk:
+        for kind in ("ffma", "ffma2", "dfma"):
+            vals = [ads.ads.measure_fma_peak(kind, local, 1 << 15 if kind == "dfma" else 1 << 17)[0]
+                    for _ in range(3)]
+            out[kind + "_tflops"] = round(max(vals), 2)
+    out["clocks"] = clk.summary()
+    return out
 
 
 def dist_env():
@@ -256,9 +282,18 @@ def run_ours(args):
     step_gbs = interior * NSTEPS * args.steps * (28 + 4 / 16) / t_dev / 1e9
     roofline["step"] = {"bytes_per_interior_dof": 28.25, "achieved": round(step_gbs, 1),
                         "frac": round(step_gbs / peak, 4)}
+    if dom == "rhs_xy_sweep" and rhs_by_p:
+        # K1's arithmetic rate against the FP32 FMA peak (computed after the
+        # peaks are measured, below)
+        k1_fl = [step_flops(s.p)["k1_fused"] * (s.n[0] - 2) * (s.n[1] - 2) * (s.n[2] - 2) /
+                 (rhs_by_p["rhs_xy_sweep_p%d" % s.p] / 1e3) / 1e12 for s in sims]
+        roofline["k1_tflops_by_p"] = {"p%d" % s.p: round(v, 3) for s, v in zip(sims, k1_fl)}
 
-    # ---- accuracy of the FP32 path against the FP64 path (fresh runs)
+    # ---- accuracy of both paths against the FP64 CPU oracle (fresh runs of
+    # the whole configuration, 200 steps); the oracle runs in a thread during
+    # the device-timed batch and elasticity measurements below
     acc = {}
+    finals = {}
     s64 = make_sims("fp64", torch, ads, wl, stream)
     s32 = make_sims("fp32", torch, ads, wl, stream)
     for a, b in zip(s64, s32):
@@ -266,6 +301,7 @@ def run_ours(args):
         b.step(NSTEPS)
         ua = a.get_state(fields=("u",))[0]
         ub = b.get_state(fields=("u",))[0]
+        finals[a.p] = (ua, ub)
         acc["p%d" % a.p] = float(np.linalg.norm(ub - ua) / np.linalg.norm(ua))
 
     # ---- FP64 path throughput (same workload, fewer steps)
@@ -285,6 +321,16 @@ def run_ours(args):
         e1.synchronize()
         t64 += e0.elapsed_time(e1) / 1e3
     fp64 = {"value": dof_steps * k64 / t64, "ms_per_step": t64 / k64 * 1e3, "steps": k64}
+    peaks_cc = measure_peaks(ads, local) if not args.no_peaks else {}
+    # the FP64 path against the DFMA peak: algorithmic FLOPs of the step per
+    # interior unknown times interior DOF-steps over the device time
+    fl64 = sum(step_flops(s.p)["step"] * (s.n[0] - 2) * (s.n[1] - 2) * (s.n[2] - 2) for s in s64) * NSTEPS * k64
+    if peaks_cc.get("dfma_tflops"):
+        ach = fl64 / t64 / 1e12
+        fp64["roofline"] = {"bound": "alu", "achieved": round(ach, 3), "peak": peaks_cc["dfma_tflops"],
+                            "unit": "TFLOP/s", "frac": round(ach / peaks_cc["dfma_tflops"], 4),
+                            "peak_source": "measured (ads_measure_fma_peak, DFMA)",
+                            "flops_per_interior_dof_step": {"p%d" % p: step_flops(p)["step"] for p in PS}}
 
     # ---- end to end through the C ABI with pinned host buffers
     host = []
@@ -322,10 +368,18 @@ def run_ours(args):
         "fp64": fp64, "rel_l2_fp32_vs_fp64_u": acc,
         "roofline": roofline, "clocks": clk.summary(),
     }
+    if peaks_cc:
+        out["peaks_measured"] = peaks_cc
+        if "k1_tflops_by_p" in roofline and peaks_cc.get("ffma2_tflops"):
+            roofline["k1_frac_of_ffma2"] = {k: round(v / peaks_cc["ffma2_tflops"], 4)
+                                            for k, v in roofline["k1_tflops_by_p"].items()}
+    oracle_job = OracleFinals(PS, NSTEPS) if (rank == 0 and not args.no_oracle_check) else None
     if not args.no_batch:
         out["batch"] = guarded(run_batch, args, stream, flush)
     if not args.no_elastic:
         out["elastic"] = guarded(run_elastic, args, stream, flush)
+    if oracle_job is not None:
+        out["rel_l2_vs_oracle"] = guarded(oracle_job.compare, finals)
     if not args.no_serve:
         out["serving"] = guarded(run_serving, args)
     if rank == 0 and not args.no_cpu_baseline:
@@ -374,11 +428,45 @@ def run_batch(args, stream, flush):
         e1.synchronize()
         t += e0.elapsed_time(e1) / 1e3
     n = sum(dofs(s) for s in sims)
+    interior = sum((s.n[0] - 2) * (s.n[1] - 2) * (s.n[2] - 2) for s in sims)
+    # kernel shares: each member's kernels timed by CUDA events in one profiled
+    # step of its own (ads_profile_step), summed over the members
+    kms = {}
+    for s in sims:
+        for name, ms in s.profile_step():
+            kms[name] = kms.get(name, 0.0) + ms
+    tot = sum(kms.values())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = None   # ncu DRAM bytes per interior DOF-step of K1 + K3 on an L2-exceeding batch
+    try:
+        import glob
+        for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+            for line in open(path):
+                f = line.split()
+                if len(f) == 3 and f[0] == "traffic_bytes_per_interior_dof_step" and f[1] == "batch":
+                    traffic = float(f[2])
+    except Exception:
+        pass
+    rate = interior * 50 * reps / t   # interior DOF-steps/s
+    roof = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": "measured" if peaks else "fallback",
+            "state_bytes_per_interior_dof_step": 16,
+            "achieved_state": round(rate * 16 / 1e9, 1), "frac_state": round(rate * 16 / 1e9 / peak, 4),
+            "two_pass_bytes_per_interior_dof_step": 28,
+            "achieved_two_pass": round(rate * 28 / 1e9, 1), "frac_two_pass": round(rate * 28 / 1e9 / peak, 4),
+            "kernel_share": {k: round(v / tot, 4) for k, v in kms.items()},
+            "traffic_bytes_per_interior_dof_step": traffic,
+            "footprint_bytes": int(sum(s.device_bytes for s in sims))}
     for s in sims:
         s.close()
     return {"value": dof_steps * reps / t, "unit": UNIT, "simulations": len(cases), "steps_each": 50,
-            "total_dofs": n, "reps": reps, "ms_per_rep": t / reps * 1e3,
+            "total_dofs": n, "interior_dofs": interior, "reps": reps, "ms_per_rep": t / reps * 1e3,
             "tiles_fused": sum(1 for s, r in zip(cases, tiles) if r == s.n_elem[1] + s.p - 2),
+            "roofline": roof,
             "workload": "batch64_pwave_uneven_32to160_p2p3_50steps_fp32"}
 
 
@@ -470,6 +558,88 @@ class OracleRunner:
         return self.ora.num_threads()
 
 
+class OracleFinals:
+    """The benchmark workload run to its end by the FP64 CPU oracle (in a
+    thread: the oracle's C loops release the interpreter), for the error of
+    the GPU paths against it."""
+
+    def __init__(self, degrees, steps):
+        self.result, self.error = {}, None
+        self.t = threading.Thread(target=self._run, args=(degrees, steps), daemon=True)
+        self.t.start()
+
+    def _run(self, degrees, steps):
+        try:
+            r = OracleRunner(degrees)
+            for m in r.sims:
+                u, v, a = m["s"].pwave_run(*m["state"], m["tau"], steps, step0=0, G=m["G"])
+                self.result[m["s"].p] = m["s"].pad(u)
+        except Exception as e:   # noqa: BLE001
+            self.error = e
+
+    def compare(self, finals):
+        self.t.join()
+        if self.error:
+            raise self.error
+        out = {"steps": NSTEPS}
+        for p, (u64, u32) in finals.items():
+            ref = self.result[p]
+            nr = float(np.linalg.norm(ref))
+            out["fp64_p%d" % p] = float(np.linalg.norm(u64 - ref) / nr)
+            out["fp32_p%d" % p] = float(np.linalg.norm(u32 - ref) / nr)
+        return out
+
+
+def cpu_table(args):
+    """The oracle timed per configuration at 1 thread and at all cores
+    (bounded samples of Newmark steps; set-up not timed): DOF-steps/s."""
+    import oracle as ora
+    from paper_1911_08158_gb300 import workloads as wl
+    allc = ora.num_threads()
+    rows = []
+
+    def time_wave(case, steps):
+        s = ora.Space(case.n_elem, case.p)
+        G = None
+        if case.source:
+            G = s.load_gauss(case.source["amp"], case.source["center"], case.source["den"])
+        u = s.project_gauss(case.u0["amp"], case.u0["center"], case.u0["den"]) if case.u0 else s.zeros()
+        z = s.zeros()
+        a = s.pwave_accel(u, 0.0, 1.0, G)
+        out = {}
+        for th in (1, allc):
+            ora.set_num_threads(th)
+            t0 = time.perf_counter()
+            s.pwave_run(u, z, a, case.tau, steps, step0=0, G=G)
+            out[th] = (int(np.prod(s.n)) * steps / (time.perf_counter() - t0), steps)
+        return out
+
+    def time_elastic(case, steps):
+        s = ora.Space(case.n_elem, case.p)
+        g = s.project_gauss(case.v0["amp"], case.v0["center"], case.v0["den"])
+        V0 = np.stack([case.v0["dir"][i] * g for i in range(3)])
+        U0 = np.zeros_like(V0)
+        Up = s.elastic_start(case.tau, case.lam, case.mu, case.rho, U0, V0)
+        out = {}
+        for th in (1, allc):
+            ora.set_num_threads(th)
+            t0 = time.perf_counter()
+            s.elastic_run(case.tau, case.lam, case.mu, case.rho, steps, U0, Up, step0=0)
+            out[th] = (3 * int(np.prod(s.n)) * steps / (time.perf_counter() - t0), steps)
+        return out
+
+    for name, fn, case, steps in (
+            ("C1 16^3 p=2 FP64 pulse", time_wave, wl.pulse_case(ne=16, p=2, tau=1e-2, steps=20), 20),
+            ("C2 128^3 p=2 Ricker", time_wave, wl.ricker_case(ne=NE, p=2), args.cpu_table_steps),
+            ("C2 128^3 p=3 Ricker", time_wave, wl.ricker_case(ne=NE, p=3), args.cpu_table_steps),
+            ("C3 96^3 p=2 elasticity", time_elastic, wl.elastic_case(), args.cpu_table_steps)):
+        r = fn(case, steps)
+        rows.append({"config": name, "threads_1": round(r[1][0]), "threads_all": round(r[allc][0]),
+                     "steps_timed": steps, "cores": allc})
+    ora.set_num_threads(allc)
+    print(json.dumps({"cpu_table": rows, "unit": UNIT, "kind": "oracle", "cores": allc}))
+
+
 def cpu_baseline(seconds: float):
     r = OracleRunner()
     dofs, n, t = r.run(seconds)
@@ -546,13 +716,21 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-elastic", action="store_true", help="skip the elasticity measurement")
     ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--no-peaks", action="store_true", help="skip the CUDA-core FMA peak measurement")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the error of the 200-step runs against the CPU oracle")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the CPU oracle per configuration at 1 thread and all cores, print, exit")
+    ap.add_argument("--cpu-table-steps", type=int, default=4)
     ap.add_argument("--autotune-steps", type=int, default=3,
                     help="trial steps per K1 layout candidate (0: take the first candidate)")
     ap.add_argument("--profile-case", default="", help="run a small case (n or nx,ny,nz elements) for ncu and exit")
     ap.add_argument("--profile-p", type=int, default=2)
     ap.add_argument("--profile-batch", type=int, default=1, help="simulations advanced together in the profile case")
     args = ap.parse_args()
-    if args.profile_case:
+    if args.cpu_table:
+        cpu_table(args)
+    elif args.profile_case:
         ne = tuple(int(v) for v in args.profile_case.split(","))
         profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4, args.profile_batch)
     elif args.impl == "reference":

@@ -94,6 +94,7 @@ def lib():
                                                 ctypes.c_double, ctypes.c_double, _D, _D]
             L.ora_elastic_invariant.restype = ctypes.c_double
             L.ora_num_threads.restype = ctypes.c_int
+            L.ora_set_num_threads.argtypes = [ctypes.c_int]
         return _lib
 
 
@@ -142,6 +143,11 @@ def ricker(f: float, t0: float, t: float) -> float:
 
 def num_threads() -> int:
     return lib().ora_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (timing only)."""
+    lib().ora_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- 3D space

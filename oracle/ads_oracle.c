@@ -810,3 +810,14 @@ int ora_num_threads(void)
     return 1;
 #endif
 }
+
+/* threads of the OpenMP loops from now on (n >= 1); timing only, the
+ * arithmetic and its order do not depend on it */
+void ora_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -233,3 +233,39 @@ def test_concurrent_host_threads():
     assert not errors
     for s, ref in zip(sims, seq):
         assert np.array_equal(s.get_state()[0], ref)
+
+
+def test_batch64_largest_members_match_oracle_50_steps():
+    """The batched configuration at its full size, in the launch
+    configuration the benchmark times: the 64 seeded uneven simulations
+    (elements per axis U{32..160}, p in {2, 3}, Gaussian pulses), FP32,
+    autotuned K1 layouts, advanced together for their 50 steps by
+    ads_batch_step.  The largest p = 2 and p = 3 members are compared with
+    the oracle element-wise (FP32 tolerance).  Every member is checked by a
+    property that holds at any size: with f = 0 the scheme conserves its
+    modified energy exactly for n >= 1 (Sec. 3), so the FP32 members' FP64
+    energy after 50 steps equals that after step 1 up to FP32 rounding
+    (bound 1e-3 relative, far above the ~1e-6 that rounding of the state
+    gives, far below what a wrong or skipped member would give)."""
+    from paper_1911_08158_gb300 import batch_step
+    cases = wl.batch_cases(count=64, seed=0, steps=50)
+    sims = [_make(c, "fp32") for c in cases]
+    for s in sims:
+        s.autotune(3)
+    batch_step(sims, 1)
+    e1 = [sum(s.energy()[1:]) for s in sims]
+    batch_step(sims, 49)
+    size = [c.n_elem[0] * c.n_elem[1] * c.n_elem[2] for c in cases]
+    picks = [max((i for i in range(len(cases)) if cases[i].p == p), key=lambda i: size[i]) for p in (2, 3)]
+    for i, (c, s) in enumerate(zip(cases, sims)):
+        assert s.step_count == 50
+        e50 = sum(s.energy()[1:])
+        assert e1[i] > 0 and abs(e50 - e1[i]) <= 1e-3 * e1[i], (c.n_elem, c.p, e1[i], e50)
+    for i in picks:
+        c, s = cases[i], sims[i]
+        ref = oracle_wave(c, 50)[50]
+        got = s.get_state()
+        check_state(got, ref, "fp32", c.tau, 1e-5, "batch member %s p=%d" % (c.n_elem, c.p))
+        print("C4 member %s p=%d rel-L2 u %.3e" % (c.n_elem, c.p,
+                                                    np.linalg.norm(got[0] - ref[0]) / np.linalg.norm(ref[0])))
+

@@ -75,12 +75,15 @@ def test_elastic_checkpoint_bitwise(precision):
         assert np.array_equal(x, y)
 
 
-def test_96cubed_elasticity_10_steps():
-    """The elasticity configuration's size (96^3 elements, p = 2, three
-    components, tau = 2e-3), 10 steps, FP32 and FP64 against the oracle."""
-    case = wl.elastic_case(ne=96, p=2, tau=2e-3, steps=10)
-    ref = oracle_elastic(case, 10)
+def test_96cubed_elasticity_100_steps():
+    """The elasticity configuration at its full size and length (96^3
+    elements, p = 2, three components, tau = 2e-3, 100 steps, seeded vector
+    Gaussian velocity pulse), FP64 and FP32 against the oracle after 10 and
+    after 100 steps."""
+    case = wl.elastic_case(ne=96, p=2, tau=2e-3, steps=100)
+    ref = oracle_elastic(case, 100, checkpoints=(10,))
     for precision in ("fp64", "fp32"):
-        _, got = gpu_elastic(case, 10, precision)
-        _check(got[10], ref[10], precision, case.tau, 10, precision)
-        print("96^3 elasticity %s rel-L2 U at 10: %.3e" % (precision, rel_l2(got[10][0], ref[10][0])))
+        _, got = gpu_elastic(case, 100, precision, checkpoints=(10,))
+        for n in (10, 100):
+            _check(got[n], ref[n], precision, case.tau, n, "%s step %d" % (precision, n))
+            print("96^3 elasticity %s rel-L2 U at %d: %.3e" % (precision, n, rel_l2(got[n][0], ref[n][0])))

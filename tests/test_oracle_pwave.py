@@ -206,3 +206,23 @@ def test_standing_wave_converges_in_space_at_order_p_plus_1(p, nes, T, N):
     rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert abs(rates[-1] - (p + 1)) < 0.2, (errs, rates)
     assert all(p + 1 - 0.2 < r < p + 1 + 0.5 for r in rates), (errs, rates)
+
+
+def test_thread_count_does_not_change_results():
+    """The oracle's OpenMP loops run over independent lines: 1 thread and all
+    threads give bitwise equal steps (the benchmark times both)."""
+    from paper_1911_08158_gb300 import workloads as wl
+    case = wl.ricker_case(ne=(14, 12, 10), p=3, tau=2e-3, steps=3, seed=3, sigma=0.08)
+    s = ora.Space(case.n_elem, case.p)
+    G = s.load_gauss(case.source["amp"], case.source["center"], case.source["den"])
+    z = s.zeros()
+    a = s.pwave_accel(z, 0.0, 1.0, G)
+    allc = ora.num_threads()
+    try:
+        ora.set_num_threads(1)
+        one = s.pwave_run(z, z, a, case.tau, 3, step0=0, G=G)
+    finally:
+        ora.set_num_threads(allc)
+    many = s.pwave_run(z, z, a, case.tau, 3, step0=0, G=G)
+    for x, y in zip(one, many):
+        assert np.array_equal(x, y)
