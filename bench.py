@@ -677,11 +677,11 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def profile_case(ne, p: int, steps: int, batch: int = 1):
+def profile_case(ne, p: int, steps: int, batch: int = 1, tune: int = 3):
     """Small fixed case for ncu captures: `batch` FP32 simulations of ne
-    (n or nx,ny,nz) elements with autotuned K1 layouts, advanced together
-    (grouped launches; no timing): two warm-up steps, then `steps` single
-    steps."""
+    (n or nx,ny,nz) elements with autotuned K1 layouts (tune = 0: the first
+    candidate, no timed trials), advanced together (grouped launches; no
+    timing): two warm-up steps, then `steps` single steps."""
     import torch
 
     import paper_1911_08158_gb300 as ads
@@ -694,7 +694,7 @@ def profile_case(ne, p: int, steps: int, batch: int = 1):
         sim = ads.Simulation(case.n_elem, case.p, case.tau, precision="fp32")
         sim.set_source(case.source)
         sim.set_gaussian_state(None, None)
-        sim.autotune(3)   # the layout the benchmark would use
+        sim.autotune(tune)   # the layout the benchmark would use (tune = 3)
         sims.append(sim)
     ads.batch_step(sims, 2)
     for _ in range(steps):
@@ -727,12 +727,13 @@ def main():
     ap.add_argument("--profile-case", default="", help="run a small case (n or nx,ny,nz elements) for ncu and exit")
     ap.add_argument("--profile-p", type=int, default=2)
     ap.add_argument("--profile-batch", type=int, default=1, help="simulations advanced together in the profile case")
+    ap.add_argument("--profile-tune", type=int, default=3, help="autotuner trial steps in the profile case")
     args = ap.parse_args()
     if args.cpu_table:
         cpu_table(args)
     elif args.profile_case:
         ne = tuple(int(v) for v in args.profile_case.split(","))
-        profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4, args.profile_batch)
+        profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4, args.profile_batch, args.profile_tune)
     elif args.impl == "reference":
         run_reference(args)
     else:

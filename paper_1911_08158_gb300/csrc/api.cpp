@@ -69,6 +69,9 @@ struct TableSet {
     void *gband[3] = {};                       // bands of M + eta c2 K (energies)
     void *src[3] = {};                         // separable source load vectors
     void *srcfield = nullptr;                  // general source load vector (interior layout)
+    // fused elastic step (Dirichlet): the elastic K1 images [lower/upper][i]
+    void *elimg[2][3] = {};
+    int elimg_bytes[2][3] = {};
 };
 
 struct ads_sim {
@@ -101,6 +104,8 @@ struct ads_sim {
     // kernel tiling of K1 per precision
     int ty[2] = {0, 0}, tz[2] = {0, 0}, fuse[2] = {0, 0};
     int pair[2] = {0, 0};   // FP32: K1 as a 2-CTA cluster per z-plane
+    int ty_el[2] = {0, 0};  // rows per tile of the elastic K1 (three planes), per precision
+    bool fused_el = false;  // elasticity: the fused alternating-triangular step
     int seg = 32;           // register segment width of the line solves
     // graphs: chunk size -> executable graph, and the kernels it launches
     std::map<int, cudaGraphExec_t> graphs;
@@ -256,6 +261,41 @@ int upload_rhs_image(ads_sim *s, TableSet &ts, int slot, int xset, int yset)
     return upload_padded<T>(s, img, &ts.img[slot], &ts.img_bytes[slot]);
 }
 
+// c_{i,a} of the diagonal block Ups_ii = sum_a c_ia [K on axis a, M elsewhere]
+double el_coef(const ads_sim *s, int i, int a) { return s->mu + (a == i ? s->lam + s->mu : 0.0); }
+
+// Elastic K1 image of component i, kind 0 (lower sweep) or 1 (upper):
+//   bMx | X1 | bMy | bKy | fx | fy | x tables | y tables | Bx
+// X1 = Kx (lower: the diagonal block of Ups U; the kernel scales the
+// contraction by -tau^2/rho c_i0) or Mx (upper: rho M y / rho); factor sets
+// ELAS0 on axis i, ELAS1 elsewhere.
+template <typename T>
+int upload_el_image(ads_sim *s, TableSet &ts, int kind, int i)
+{
+    const int xset = i == 0 ? SET_ELAS0 : SET_ELAS1, yset = i == 1 ? SET_ELAS0 : SET_ELAS1;
+    if (s->hline[xset][0].empty() || s->hline[yset][1].empty()) return ADS_OK;
+    std::vector<double> img;
+    auto add = [&](const std::vector<double> &v) { img.insert(img.end(), v.begin(), v.end()); };
+    add(s->hM[0]);
+    add(kind == 0 ? s->hK[0] : s->hM[0]);
+    add(s->hM[1]);
+    add(s->hK[1]);
+    for (int a = 0; a < 2; ++a) {
+        const size_t mp = (size_t)padded(s, s->ax[a].m);
+        if (s->hsrc[a].size() == mp) add(s->hsrc[a]);
+        else img.insert(img.end(), mp, 0.0);
+    }
+    add(s->hline[xset][0]);
+    add(s->hline[yset][1]);
+    const ads::Axis1D &ax = s->ax[0];
+    add(pad_rows(ax.B.v, ax.m, 2 * ax.p + 1, padded(s, ax.m), false));
+    if (ts.elimg[kind][i]) {
+        dfree(s, ts.elimg[kind][i]);
+        ts.elimg[kind][i] = nullptr;
+    }
+    return upload_padded<T>(s, img, &ts.elimg[kind][i], &ts.elimg_bytes[kind][i]);
+}
+
 // every K1 image of a table set
 template <typename T>
 int upload_rhs_images(ads_sim *s, TableSet &ts)
@@ -270,6 +310,12 @@ int upload_rhs_images(ads_sim *s, TableSet &ts)
                                          i == 1 ? SET_ELAS0 : SET_ELAS1);
             if (rc) return rc;
         }
+    if (s->fused_el)
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 2; ++k) {
+                int rc = upload_el_image<T>(s, ts, k, i);
+                if (rc) return rc;
+            }
     return ADS_OK;
 }
 
@@ -369,6 +415,17 @@ void choose_tiles(ads_sim *s)
         s->ty[pi] = ty;
         s->tz[pi] = 1;
         s->fuse[pi] = (ty == my) ? 1 : 0;
+        // the elastic K1 holds a third plane (and Bx): the whole plane when it
+        // fits, else row tiles followed by a y sweep
+        auto fits3 = [&](int t, size_t b) {
+            return ads::rhs_smem_bytes(s->p, el, s->d, t, Sx, Sy, s->seg, 0, 3) <= b;
+        };
+        int te = my;
+        if (!fits3(te, budget_fused)) {
+            te = std::min(my, 32);
+            while (te > 1 && !fits3(te, budget)) te /= 2;
+        }
+        s->ty_el[pi] = te;
     }
 }
 
@@ -847,8 +904,12 @@ int add_body_force(ads_sim *s, T *r, double scale, int toff)
 //   D = (rho M + tau^2/2 Ups1~) (rho M)^{-1} (rho M + tau^2/2 Ups2~),
 // block-lower solve, rho M, block-upper solve, U^{n+1} = 2U^n - U^{n-1} + delta.
 template <typename T>
+int elastic_step_fused(ads_sim *s, KernelTimer *kt);
+
+template <typename T>
 int elastic_step(ads_sim *s, KernelTimer *kt = nullptr)
 {
+    if (s->fused_el) return elastic_step_fused<T>(s, kt);
     const long long cnt = s->d.count();
     T *U = (T *)s->U, *Up = (T *)s->Up, *R = (T *)s->R, *Y = (T *)s->Y;
     const T tau2 = (T)(s->tau * s->tau), rho = (T)s->rho;
@@ -877,6 +938,107 @@ int elastic_step(ads_sim *s, KernelTimer *kt = nullptr)
         for (int j = i + 1; j < 3; ++j) add_offdiag<T>(s, ks, i, j, R + j * cnt, -hr);
         ADS_CK(ads::launch_kron_sum<T>(s->p, ks, R + i * cnt, s->d, s->stream));
         if ((rc = elastic_diag_solve<T>(s, i, R + i * cnt))) return rc;
+    }
+    if (kt && (rc = kt->mark(s->stream, "elastic_update"))) return rc;
+    ADS_CK(ads::launch_atm_update<T>(U, Up, R, 3 * cnt, s->d_step, s->stream));
+    if (kt && (rc = kt->mark(s->stream, ""))) return rc;
+    return ADS_OK;
+}
+
+// Fused alternating-triangular step (Dirichlet): every diagonal-block solve
+// is one elastic K1 (the block's right-hand side by sum factorisation, with
+// the off-diagonal blocks Ups_ij of the other components as extra Kronecker
+// terms, then the x [and y] sweeps) and one z sweep:
+//   lower, i = 0, 1, 2:  rhs_i = tau^2/rho (f_i - sum_j Ups_ij U^n_j)
+//                                - tau^2/(2 rho) sum_{j<i} Ups_ij y_j,
+//                        y_i = L~_i^{-1} rhs_i
+//   upper, i = 2, 1, 0:  rhs_i = M y_i - tau^2/(2 rho) sum_{j>i} Ups_ij delta_j,
+//                        delta_i = L~_i^{-1} rhs_i
+//   U^{n+1} = 2U^n - U^{n-1} + delta
+// (eqs. decom, pre, corr, spill, gen with sigma = 1/2; L~_i has the factored
+// blocks of eq. spill scaled by 1/rho).  Ups_ij (i != j) = -(mu + lam)
+// [B on axes i and j, M on the third].  13 launches per step.
+template <typename T>
+int elastic_block_solve(ads_sim *s, int kind, int i, const T *main_in, T *out, const ads::RhsElas<T> &el)
+{
+    const TableSet &ts = tables_for<T>(s);
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    auto set = [&](int a) { return a == i ? SET_ELAS0 : SET_ELAS1; };
+    ads::RhsArgs<T> r = rhs_args<T>(s, main_in, out, set(0), 0, kind == 0);
+    r.ly = line_dev<T>(ts.line[set(1)][1]);
+    r.img = (const T *)ts.elimg[kind][i];
+    r.img_bytes = ts.elimg_bytes[kind][i];
+    r.c2 = T(-1);
+    r.ty = s->ty_el[pi];
+    r.pair = 0;
+    r.direct = 0;
+    // body force of component i at level n: tau^2/rho r(t_n) dir_i g
+    r.src.amp = s->tau * s->tau / s->rho * s->src.shape.dir[i];
+    ADS_CK(ads::launch_rhs_el<T>(s->p, r, el, s->stream));
+    ads::ColArgs<T> c{};
+    c.d = s->d;
+    c.mode = 0;
+    c.in = out;
+    c.out = out;
+    c.err = s->d_err;
+    if (r.ty != s->d.my) {
+        c.axis = 1;
+        c.ln = line_dev<T>(ts.line[set(1)][1]);
+        ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    }
+    c.axis = 2;
+    c.ln = line_dev<T>(ts.line[set(2)][2]);
+    ADS_CK(ads::launch_col<T>(s->p, s->seg, c, s->stream));
+    return ADS_OK;
+}
+
+// the off-diagonal block Ups_ij applied to `in`, coef times, as an extra term
+// of component i's elastic K1: B on axes i and j, M on the third
+template <typename T>
+void add_extra(const ads_sim *s, ads::RhsElas<T> &el, int i, int j, const T *in, double coef)
+{
+    const TableSet &ts = tables_for<T>(s);
+    auto band = [&](int a) { return (const T *)((a == i || a == j) ? ts.B[a] : ts.M[a]); };
+    ads::ExtraTerm<T> &e = el.ex[el.n++];
+    e.in = in;
+    e.by = band(1);
+    e.bz = band(2);
+    e.coef = (T)(coef * -(s->lam + s->mu));
+    e.slot = (i == 0 || j == 0) ? 3 : 2;
+    e.init = 0;
+    if (e.slot == 3 && !el.s3) {
+        el.s3 = 1;
+        e.init = 1;
+    }
+}
+
+template <typename T>
+int elastic_step_fused(ads_sim *s, KernelTimer *kt)
+{
+    const long long cnt = s->d.count();
+    T *U = (T *)s->U, *Up = (T *)s->Up, *R = (T *)s->R, *Y = (T *)s->Y;
+    const double g = s->tau * s->tau / s->rho, h = 0.5 * g;
+    int rc;
+    if (kt && (rc = kt->mark(s->stream, "elastic_lower"))) return rc;
+    for (int i = 0; i < 3; ++i) {
+        ads::RhsElas<T> el{};
+        // the diagonal block -tau^2/rho Ups_ii U_i, Ups_ii = sum_a c_ia [K on axis a]
+        el.cx = (T)(-g * el_coef(s, i, 0));
+        el.cy = (T)(-g * el_coef(s, i, 1));
+        el.cz = (T)(-g * el_coef(s, i, 2));
+        for (int j = 0; j < 3; ++j)
+            if (j != i) add_extra<T>(s, el, i, j, U + j * cnt, -g);   // -tau^2/rho Ups_ij U_j
+        for (int j = 0; j < i; ++j) add_extra<T>(s, el, i, j, Y + j * cnt, -h);
+        if ((rc = elastic_block_solve<T>(s, 0, i, U + i * cnt, Y + i * cnt, el))) return rc;
+    }
+    if (kt && (rc = kt->mark(s->stream, "elastic_upper"))) return rc;
+    for (int i = 2; i >= 0; --i) {
+        ads::RhsElas<T> el{};
+        el.cx = T(1);   // M y_i: X1 = Mx, no K part
+        el.cy = T(0);
+        el.cz = T(0);
+        for (int j = i + 1; j < 3; ++j) add_extra<T>(s, el, i, j, R + j * cnt, -h);
+        if ((rc = elastic_block_solve<T>(s, 1, i, Y + i * cnt, R + i * cnt, el))) return rc;
     }
     if (kt && (rc = kt->mark(s->stream, "elastic_update"))) return rc;
     ADS_CK(ads::launch_atm_update<T>(U, Up, R, 3 * cnt, s->d_step, s->stream));
@@ -1421,6 +1583,12 @@ int ads_create(const ads_grid_t *grid, int p, double tau, const ads_material_t *
     s->d.sx = (s->d.mx + 7) / 8 * 8;
     s->d.off = grid->boundary == ADS_NATURAL ? 0 : 1;
     s->d.offz = plane2d ? 0 : s->d.off;
+    // elasticity with the Dirichlet restriction takes the fused step (its
+    // off-diagonal blocks are single Kronecker terms); the natural boundary
+    // keeps the step through the Kronecker-sum kernel
+    s->fused_el = s->kind == ADS_ELASTIC && s->d.off == 1;
+    if (const char *env = std::getenv("ADS_ELASTIC_STEP"))   // "kron": the unfused step, for comparisons
+        if (std::strcmp(env, "kron") == 0) s->fused_el = false;
     {
         const int m3[3] = {s->d.mx, s->d.my, s->d.mz};
         // 33-row segments when they save segments (m = 32 s + 1), 44 when they save K1 rounds
@@ -1979,6 +2147,12 @@ size_t ads_estimate_bytes(const ads_grid_t *grid, int p, int kind, int precision
         for (int k = 0; k < nimg; ++k)
             add(2 * (mp[0] + mp[1]) * W * e + (mp[0] + mp[1]) * e +
                 (ads::line_image_elems(p, (int)S[0], seg) + ads::line_image_elems(p, (int)S[1], seg)) * e + 64);
+        if (kind == ADS_ELASTIC && grid->boundary != ADS_NATURAL) {
+            // fused step: six elastic K1 images (with Bx)
+            for (int k = 0; k < 6; ++k)
+                add((3 * mp[0] + 2 * mp[1]) * W * e + (mp[0] + mp[1]) * e +
+                    (ads::line_image_elems(p, (int)S[0], seg) + ads::line_image_elems(p, (int)S[1], seg)) * e + 64);
+        }
     }
     return b;
 }

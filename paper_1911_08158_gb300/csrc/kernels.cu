@@ -485,11 +485,13 @@ size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy, int seg)
            line_image_elems(p, Sy, seg);
 }
 
-size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg, int pair)
+size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg, int pair, int planes)
 {
     const RhsPlan q = rhs_plan(d.mx, d.my, ty, pair, Sx, Sy);
-    size_t n = 2 * (size_t)q.rows * q.RS + 2 * (size_t)q.Smax * p * q.cld;
-    return n * elem + 16 + ((rhs_image_elems(p, d, Sx, Sy, seg) * elem + 15) & ~(size_t)15);
+    size_t n = (size_t)planes * q.rows * q.RS + 2 * (size_t)q.Smax * p * q.cld;
+    size_t img = rhs_image_elems(p, d, Sx, Sy, seg);
+    if (planes == 3) img += (size_t)Sx * seg * (2 * p + 1);   // Bx
+    return n * elem + 16 + ((img * elem + 15) & ~(size_t)15);
 }
 
 namespace {

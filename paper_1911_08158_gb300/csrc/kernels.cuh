@@ -86,6 +86,39 @@ struct RhsArgs {
     int pair;             // 1 (FP32): a 2-CTA cluster per z-plane (fused y sweep across the pair)
 };
 
+// Extra Kronecker terms of the elastic right-hand side (the off-diagonal
+// blocks of Sec. 5): coef (Ay (x) Az) in, contracted along z and y in K1's
+// phase 1 and accumulated into plane `slot` (2: contracted along x with the
+// image's second x band, M; 3: with the third, B), so that K1 forms
+//   R = F - c2 (X1 s1 + Mx s2 + Bx s3)
+// with s1, s2 from the stream of `in` (the diagonal block) and the extra
+// terms inside s2, s3.
+template <typename T>
+struct ExtraTerm {
+    const T *in;
+    const T *by, *bz;   // bands [m_pad][2p+1] along y and z
+    T coef;
+    int slot;           // 2 or 3
+    int init;           // 1: the first term of plane 3 writes it
+};
+constexpr int kMaxExtra = 4;
+template <typename T>
+struct RhsElas {
+    ExtraTerm<T> ex[kMaxExtra];
+    int n;
+    int s3;             // 1: plane 3 exists (some term has slot 3); the image then ends with Bx [mxp][2p+1]
+    // coefficients of the stream of `in`, applied after each contraction so
+    // that the bands keep their exact row sums:
+    //   s2 = cy (Ky Mz in) + cz (My Kz in),  R = F - c2 (cx X1 s1 + Mx s2 + Bx s3)
+    T cx, cy, cz;
+};
+// one elastic K1 launch (a single simulation)
+template <typename T>
+struct RhsElGroup {
+    RhsArgs<T> a;
+    RhsElas<T> el;
+};
+
 // Column sweep along y (axis 1) or z (axis 2): 32 x-columns per CTA, one
 // warp per line segment.
 //   mode 0: out = A^{-1} in along the axis (in == out allowed)
@@ -140,8 +173,10 @@ struct ColGroup {
     int n;
 };
 
-// seg: register segment width of the partitioned solves (32)
-size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg, int pair = 0);
+// seg: register segment width of the partitioned solves (32); planes: the
+// s-planes of the tile (2, or 3 for the elastic K1 with a B plane, whose
+// image also holds Bx)
+size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, int seg, int pair = 0, int planes = 2);
 int rhs_threads(int elem);
 // element offsets of the K1 table image: returns total elements
 size_t rhs_image_elems(int p, const Dims &d, int Sx, int Sy, int seg);
@@ -167,6 +202,10 @@ template <typename T, int SEG>
 cudaError_t launch_rhs_seg(int p, const RhsArgs<T> *a, int n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, int n, cudaStream_t s);
+// Elastic K1 (one simulation): the diagonal block's right-hand side by sum
+// factorisation plus el's extra terms, then the x [and y] sweeps
+template <typename T>
+cudaError_t launch_rhs_el(int p, const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s);
 
 // Sum of Kronecker products in one pass:
 //   out = beta*out + sum_t alpha_t (Ax_t (x) Ay_t (x) Az_t) in_t

@@ -258,11 +258,14 @@ constexpr int kPhase1Lookahead = 1;   // stream rows whose loads are in flight a
 // and K hold zeros outside the matrix, so the loads read a clamped (valid)
 // row or plane and the zero coefficient drops its value.  zoff[k]: element
 // offset of plane clamp(z-P+k) (uniform over the CTA).
-template <typename T, int P, bool INTERIOR, int PF = kPhase1Lookahead>
+// SC (the elastic K1): s2 = cy (Ky t1) + cz (My t2), the two contractions
+// scaled after they are formed.
+template <typename T, int P, bool INTERIOR, bool SC = false, int PF = kPhase1Lookahead>
 __device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zoff)[2 * P + 1], int sx, int my,
                                              const T (&cm)[2 * P + 1], const T (&ck)[2 * P + 1],
                                              const T (&mym)[2 * P + 1], const T (&myk)[2 * P + 1], const T *bMy,
-                                             const T *bKy, int ylo, int yhi, int yb, int ye, T *s1col, T *s2col, int RS)
+                                             const T *bKy, int ylo, int yhi, int yb, int ye, T *s1col, T *s2col, int RS,
+                                             T cy = T(1), T cz = T(1))
 {
     constexpr int W = 2 * P + 1;
     using V2 = typename Vec2<T>::type;
@@ -314,14 +317,19 @@ __device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zo
                     band_row<T, W>(bMy, ylo, yhi, mym, y, bm);
                     band_row<T, W>(bKy, ylo, yhi, myk, y, bk);
                 }
-                V2 a = V2{T(0), T(0)}, c = V2{T(0), T(0)};
+                V2 a = V2{T(0), T(0)}, c = V2{T(0), T(0)}, c2 = V2{T(0), T(0)};
 #pragma unroll
                 for (int q = 0; q < W; ++q) {
                     // window row y-P+q = stream index r-2P+q  ->  ring slot (j-2P+q) mod W
                     const int sl = (j - 2 * P + q + 2 * W) % W;
                     a = fma2(bm[q], r1[sl], a);
                     c = fma2(bk[q], r1[sl], c);
-                    c = fma2(bm[q], r2[sl], c);
+                    if (SC) c2 = fma2(bm[q], r2[sl], c2);
+                    else c = fma2(bm[q], r2[sl], c);
+                }
+                if (SC) {
+                    c.x = cy * c.x + cz * c2.x;
+                    c.y = cy * c.y + cz * c2.y;
                 }
                 s1col[(size_t)y * RS] = a.x;
                 s1col[(size_t)y * RS + 1] = a.y;
@@ -334,6 +342,72 @@ __device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zo
                 for (int k = 0; k < W; ++k) pf[d][k] = pf[d + 1][k];
 #pragma unroll
             for (int k = 0; k < W; ++k) pf[PF - 1][k] = nv[k];
+        }
+    };
+    int r0 = 0;
+    for (; r0 + W <= n; r0 += W) block(r0, std::false_type{});
+    if (r0 < n) block(r0, std::true_type{});
+}
+
+// Phase 1 of the elastic K1, one extra Kronecker term for the column pair
+// (x, x+1) and output rows [yb, ye): stream the rows yp = yb-P .. ye+P-1,
+// z-contract each with the term's z band (coefficients cz of this plane)
+// into a ring of W slots, y-contract every complete window with the term's
+// y band (rows read from global memory) and add coef times the result to the
+// plane column scol (or write it: init).  Rows and planes outside the grid
+// are read clamped and meet zero band entries, as in phase1_chunk.
+template <typename T, int P>
+__device__ __forceinline__ void phase1_extra(const T *colx, const long long (&zoff)[2 * P + 1], int sx, int my,
+                                             const T *bz, const T *by, int yb, int ye, T *scol, int RS, T coef,
+                                             bool init)
+{
+    constexpr int W = 2 * P + 1;
+    using V2 = typename Vec2<T>::type;
+    T cz[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) cz[k] = bz[k];
+    V2 r[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) r[k] = V2{T(0), T(0)};
+    const int n = ye - yb + 2 * P;
+    auto load_row = [&](int rr, V2(&dst)[W]) {
+        const int yp = min(max(yb - P + rr, 0), my - 1);
+        const T *c = colx + (long long)yp * sx;
+#pragma unroll
+        for (int k = 0; k < W; ++k) dst[k] = *reinterpret_cast<const V2 *>(c + zoff[k]);
+    };
+    V2 pf[W];
+    load_row(0, pf);
+    auto block = [&](int r0, auto tail) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int rr = r0 + j;
+            if constexpr (decltype(tail)::value) {
+                if (rr >= n) break;
+            }
+            V2 nv[W];
+            load_row(rr + 1, nv);
+            V2 t = V2{T(0), T(0)};
+#pragma unroll
+            for (int k = 0; k < W; ++k) t = fma2(cz[k], pf[k], t);
+            r[j] = t;
+            if (rr >= 2 * P && rr < n) {
+                const int y = yb + rr - 2 * P;
+                const T *brow = by + (size_t)y * W;
+                V2 a = V2{T(0), T(0)};
+#pragma unroll
+                for (int q = 0; q < W; ++q) a = fma2(brow[q], r[(j - 2 * P + q + 2 * W) % W], a);
+                T *d = scol + (size_t)y * RS;
+                if (init) {
+                    d[0] = coef * a.x;
+                    d[1] = coef * a.y;
+                } else {
+                    d[0] += coef * a.x;
+                    d[1] += coef * a.y;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < W; ++k) pf[k] = nv[k];
         }
     };
     int r0 = 0;
@@ -398,6 +472,46 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
     seg_pass1<T, P, SEG>(fb, v);   // rows are independent above; the chain is here
 }
 
+// Phase 2 of the elastic K1, pass 1 for one row segment: form
+//   R = F - c2 (X1 s1 + X2 s2 [+ X3 s3])
+// with a window of 2p+1 positions per plane that slides along the segment
+// (the band rows of every position from the table), then the local forward
+// substitution.  Rows past the line end meet zero band rows and F = 0.
+template <typename T, int P, int SEG, bool HAS3>
+__device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, const T *row3, int mx, int b0,
+                                              const T *bX1, const T *bX2, const T *bX3, const T *fb, const T *fx,
+                                              T rowF, T c2, T cx, T (&v)[SEG])
+{
+    constexpr int W = 2 * P + 1;
+    T w1[W], w2[W], w3[W];
+    auto ld = [&](const T *row, int xx) { return (xx >= 0 && xx < mx) ? row[xx] : T(0); };
+#pragma unroll
+    for (int j = 0; j < 2 * P; ++j) {
+        const int xx = b0 - P + j;
+        w1[j] = ld(row1, xx);
+        w2[j] = ld(row2, xx);
+        w3[j] = HAS3 ? ld(row3, xx) : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) {
+        const int xn = b0 - P + k + 2 * P;   // the position entering the window
+        w1[(k + 2 * P) % W] = ld(row1, xn);
+        w2[(k + 2 * P) % W] = ld(row2, xn);
+        if (HAS3) w3[(k + 2 * P) % W] = ld(row3, xn);
+        const int x = b0 + k;
+        T acc1 = T(0), acc2 = T(0), acc3 = T(0);   // independent chains
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int sl = (k + q) % W;
+            acc1 += bX1[x * W + q] * w1[sl];
+            acc2 += bX2[x * W + q] * w2[sl];
+            if (HAS3) acc3 += bX3[x * W + q] * w3[sl];
+        }
+        v[k] = (fx && x < mx ? rowF * fx[x] : T(0)) - c2 * (cx * acc1 + (acc2 + acc3));
+    }
+    seg_pass1<T, P, SEG>(fb, v);
+}
+
 // ---------------------------------------------------------------- K1
 //
 // One CTA per (z-plane, y-tile of ty rows).  Shared memory: S1, S2 [ty][RS]
@@ -437,14 +551,13 @@ __device__ __forceinline__ int group_find(const int *off, int n, int b)
     return lo;
 }
 
-template <typename T, int P, int NB, int SEG, int LAYOUT>
-__global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LAYOUT>::per_sm)
-    k_rhs(const __grid_constant__ RhsGroup<T, NB> g)
+// The body of K1 for block lb of one simulation (arguments a); EL: the
+// elastic K1, whose right-hand side also holds el's extra terms (phase 1
+// accumulates them into planes 2 and 3, phase 2 contracts plane 3 with Bx).
+template <typename T, int P, int SEG, int LAYOUT, bool EL>
+__device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *el, const int lb)
 {
     constexpr bool PAIR = LAYOUT == kLayoutPair;
-    const int gs = NB > 1 ? group_find(g.off, g.n, blockIdx.x) : 0;
-    const RhsArgs<T> &a = g.a[gs];
-    const int lb = blockIdx.x - g.off[gs];   // block within this simulation
     constexpr int W = 2 * P + 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T s_r;
@@ -482,8 +595,9 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
     __shared__ __align__(8) uint64_t bar;
     T *S1 = reinterpret_cast<T *>(smem_raw);
     T *S2 = S1 + (size_t)q.rows * RS;
+    T *S3 = S2 + (size_t)q.rows * RS;   // elastic K1 with a B plane only
     const int Smax = q.Smax;
-    T *CT = S2 + (size_t)q.rows * RS;
+    T *CT = S3 + ((EL && el->s3) ? (size_t)q.rows * RS : 0);
     T *CH = CT + (size_t)Smax * P * cld;
     // the 1D tables arrive as one bulk copy into a 16-byte aligned region
     T *tb = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(CH + (size_t)Smax * P * cld) + 15) & ~(uintptr_t)15);
@@ -498,6 +612,7 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
     T *lyb = lxb + line_image_elems_dev(P, mxp, a.lx.S);
     const LineSm<T> LX = line_carve<T, P>(lxb, mxp, a.lx.S);
     const LineSm<T> LY = line_carve<T, P>(lyb, myp, a.ly.S);
+    const T *bBx = lyb + line_image_elems_dev(P, myp, a.ly.S);   // elastic images end with Bx
     const bool has_src = a.src.fx != nullptr || a.srcfield != nullptr;
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -578,10 +693,27 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
             const bool winter = __all_sync(__activemask(), inter);
             if (!live) continue;
             T *c1 = S1 + x - (size_t)y0 * RS, *c2 = S2 + x - (size_t)y0 * RS;
-            if (winter)
+            if constexpr (EL) {
+                if (winter)
+                    phase1_chunk<T, P, true, true>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb,
+                                                   ye, c1, c2, RS, el->cy, el->cz);
+                else
+                    phase1_chunk<T, P, false, true>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb,
+                                                    ye, c1, c2, RS, el->cy, el->cz);
+            } else if (winter)
                 phase1_chunk<T, P, true>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
             else
                 phase1_chunk<T, P, false>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb, ye, c1, c2, RS);
+            if constexpr (EL) {
+                // the extra terms of the same cells, after this thread's own
+                // writes of them (no barrier needed)
+                for (int t = 0; t < el->n; ++t) {
+                    const ExtraTerm<T> &e = el->ex[t];
+                    T *sc = (e.slot == 3 ? S3 : S2) + x - (size_t)y0 * RS;
+                    phase1_extra<T, P>(e.in + x, zoff, sx, my, e.bz + (size_t)z * W, e.by, yb, ye, sc, RS, e.coef,
+                                       e.init != 0);
+                }
+            }
         }
     }
     // tables in shared memory from here on; every thread leaves together if
@@ -638,7 +770,14 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
             // head rows (< kHeadRows >= Toeplitz lo) from the table; the last reads
             // every row from the table (its rows past hi are not Toeplitz)
             const bool regular = LX.S >= 2 && xlo <= kHeadRows && xhi >= (LX.S - 1) * SEG && mx >= (LX.S - 1) * SEG + P;
-            if (regular && s > 0 && s < LX.S - 1)
+            if constexpr (EL) {
+                if (el->s3)
+                    phase2_fwd_el<T, P, SEG, true>(row1, row2, S3 + (size_t)l * RS, mx, b0, bKx, bMx, bBx, fb, srcF,
+                                                   rowF, c2, el->cx, v);
+                else
+                    phase2_fwd_el<T, P, SEG, false>(row1, row2, nullptr, mx, b0, bKx, bMx, bBx, fb, srcF, rowF, c2,
+                                                    el->cx, v);
+            } else if (regular && s > 0 && s < LX.S - 1)
                 phase2_fwd<T, P, SEG, kSegMiddle>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
             else if (regular && s == 0)
                 phase2_fwd<T, P, SEG, kSegFirst>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
@@ -721,6 +860,22 @@ __global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LA
             for (int x = lane; x < mx; x += 32) dst[x] = src[x];
         }
     }
+}
+
+template <typename T, int P, int NB, int SEG, int LAYOUT>
+__global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LAYOUT>::per_sm)
+    k_rhs(const __grid_constant__ RhsGroup<T, NB> g)
+{
+    const int gs = NB > 1 ? group_find(g.off, g.n, blockIdx.x) : 0;
+    rhs_body<T, P, SEG, LAYOUT, false>(g.a[gs], nullptr, blockIdx.x - g.off[gs]);   // block within the simulation
+}
+
+// the elastic K1 of one simulation
+template <typename T, int P, int SEG, int LAYOUT>
+__global__ void __launch_bounds__(RhsThreads<T, LAYOUT>::value, RhsThreads<T, LAYOUT>::per_sm)
+    k_rhs_el(const __grid_constant__ RhsElGroup<T> g)
+{
+    rhs_body<T, P, SEG, LAYOUT, true>(g.a, &g.el, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- K2/K3
@@ -998,6 +1153,55 @@ cudaError_t rhs_seg_p(const RhsArgs<T> *a, int n, cudaStream_t s)
     return cudaSuccess;
 }
 
+// one elastic K1 launch: single-CTA layout (wide for FP64 lines of more than
+// 8 segments), never a cluster pair, never direct mode
+template <typename T, int P, int SEG, int LAYOUT>
+cudaError_t rhs_el_p(const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
+{
+    if (!rhs_entry_ok(a, SEG) || a.pair || a.direct || el.n < 0 || el.n > kMaxExtra) return cudaErrorInvalidValue;
+    if (std::max(a.lx.S, a.ty == a.d.my ? a.ly.S : 0) > RhsThreads<T, LAYOUT>::value / 32)
+        return cudaErrorInvalidValue;   // a segment without a warp
+    for (int t = 0; t < el.n; ++t)
+        if (!el.ex[t].in || !el.ex[t].by || !el.ex[t].bz || (el.ex[t].slot != 2 && el.ex[t].slot != 3) ||
+            (el.ex[t].slot == 3 && !el.s3))
+            return cudaErrorInvalidValue;
+    RhsElGroup<T> g;
+    std::memset(&g, 0, sizeof(g));
+    g.a = a;
+    g.el = el;
+    // planes, carry buffers and the table image as the kernel carves them
+    const RhsPlan q = rhs_plan(a.d.mx, a.d.my, a.ty, 0, a.lx.S, a.ly.S);
+    const size_t n = (size_t)(el.s3 ? 3 : 2) * q.rows * q.RS + 2 * (size_t)q.Smax * P * q.cld;
+    const size_t smem = n * sizeof(T) + 16 + (((size_t)a.img_bytes + 15) & ~(size_t)15);
+    static std::atomic<size_t> smem_set{48 * 1024};
+    if (cudaError_t e = raise_dyn_smem(k_rhs_el<T, P, SEG, LAYOUT>, smem_set, smem); e != cudaSuccess) return e;
+    ++g_launches;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)rhs_blocks(a), 1, 1);
+    cfg.blockDim = dim3(RhsThreads<T, LAYOUT>::value, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    std::memset(attr, 0, sizeof(attr));
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_rhs_el<T, P, SEG, LAYOUT>, g);
+}
+
+template <typename T, int P, int SEG>
+cudaError_t rhs_el_layout(const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
+{
+    const int layout = rhs_layout(a);
+    if (layout == kLayoutSingle) return rhs_el_p<T, P, SEG, kLayoutSingle>(a, el, s);
+    if constexpr (sizeof(T) == 8 && SEG != kSegLong) {
+        if (layout == kLayoutWide) return rhs_el_p<T, P, SEG, kLayoutWide>(a, el, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename T>
 bool col_entry_ok(const ColArgs<T> &a, int seg)
 {
@@ -1113,6 +1317,24 @@ cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, in
 #define C(P) col_group_dispatch<T, P>(a, maps, n, s)
     ADS_DISPATCH_P(p, C)
 #undef C
+}
+
+// the elastic K1 for every segment length (one translation unit per precision)
+template <typename T>
+cudaError_t launch_rhs_el_impl(int p, const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
+{
+    const int seg = a.lx.seg;
+    if (a.ly.seg != seg) return cudaErrorInvalidValue;
+#define C32(P) rhs_el_layout<T, P, kSeg>(a, el, s)
+#define C33(P) rhs_el_layout<T, P, kSegAlt>(a, el, s)
+#define C44(P) rhs_el_layout<T, P, kSegLong>(a, el, s)
+    if (seg == kSeg) { ADS_DISPATCH_P(p, C32) }
+    if (seg == kSegAlt) { ADS_DISPATCH_P(p, C33) }
+    if (seg == kSegLong) { ADS_DISPATCH_P(p, C44) }
+#undef C32
+#undef C33
+#undef C44
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace ads
