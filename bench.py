@@ -24,6 +24,8 @@ step; inputs stay resident in HBM.
   serving: 500 Poisson-arrival requests (20/s, 80% P-wave / 20% elasticity,
            grids log-uniform 24..256 per axis, 10..500 steps) under a 150 GB
            budget: p50/p99 latency and DOF-steps/s
+  serving_saturated: the same requests at 2000/s under a 4 GB budget
+           (admission waits on memory; the device is busy throughout)
 
 --impl reference runs the CPU oracle as the reference arm (there is no
 reference implementation of this paper; the oracle is the plain restatement).
@@ -382,6 +384,7 @@ def run_ours(args):
         out["rel_l2_vs_oracle"] = guarded(oracle_job.compare, finals)
     if not args.no_serve:
         out["serving"] = guarded(run_serving, args)
+        out["serving_saturated"] = guarded(run_serving_saturated, args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if ws > 1:
@@ -519,6 +522,24 @@ def run_serving(args):
     out = rep.summary()
     out.update(workload="serving_poisson20_%dreq_wave80_elastic20_24to256_budget150GB_fp32" % len(reqs),
                unit_latency="s", shard="rank %d of %d: %d requests" % (rank, ws, len(mine)))
+    return out
+
+
+def run_serving_saturated(args):
+    """The same 500 requests arriving 100x faster (2000 req/s: the whole
+    stream within a quarter second) under a 4 GB budget: the device is busy
+    throughout and admission waits on memory, so DOF-steps/s measures the
+    device under contention and p50/p99 include the queueing."""
+    from paper_1911_08158_gb300 import workloads as wl
+    from paper_1911_08158_gb300.serve import Server, shard_requests
+    ws, rank, _ = dist_env()
+    budget = 4 * 10 ** 9
+    reqs = wl.serving_requests(count=args.serve_requests, rate=2000.0, seed=0)
+    mine = shard_requests(reqs, rank, ws)
+    rep = Server(budget, precision="fp32", chunk=16).run(mine)
+    out = rep.summary()
+    out.update(workload="serving_poisson2000_%dreq_wave80_elastic20_24to256_budget4GB_fp32" % len(reqs),
+               unit_latency="s", budget_bytes=budget, shard="rank %d of %d: %d requests" % (rank, ws, len(mine)))
     return out
 
 
@@ -677,17 +698,28 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def profile_case(ne, p: int, steps: int, batch: int = 1, tune: int = 3):
+def profile_case(ne, p: int, steps: int, batch: int = 1, tune: int = 3, kind: str = "wave"):
     """Small fixed case for ncu captures: `batch` FP32 simulations of ne
     (n or nx,ny,nz) elements with autotuned K1 layouts (tune = 0: the first
     candidate, no timed trials), advanced together (grouped launches; no
-    timing): two warm-up steps, then `steps` single steps."""
+    timing): two warm-up steps, then `steps` single steps.  kind 'elastic':
+    one elasticity simulation (lambda = mu = rho = 1, seeded velocity pulse)."""
     import torch
 
     import paper_1911_08158_gb300 as ads
     from paper_1911_08158_gb300 import workloads as wl
 
     torch.cuda.set_device(0)
+    if kind == "elastic":
+        c = wl.elastic_case(ne=ne, p=p)
+        sim = ads.Simulation(c.n_elem, c.p, c.tau, kind="elastic", lam=c.lam, mu=c.mu, rho=c.rho, precision="fp32")
+        sim.set_gaussian_state(None, c.v0)
+        sim.step(2)
+        for _ in range(steps):
+            sim.step(1)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": ne, "p": p, "kind": kind, "steps": steps, "device_bytes": sim.device_bytes}))
+        return
     sims = []
     for i in range(batch):
         case = wl.ricker_case(ne=ne, p=p, seed=i)
@@ -728,12 +760,14 @@ def main():
     ap.add_argument("--profile-p", type=int, default=2)
     ap.add_argument("--profile-batch", type=int, default=1, help="simulations advanced together in the profile case")
     ap.add_argument("--profile-tune", type=int, default=3, help="autotuner trial steps in the profile case")
+    ap.add_argument("--profile-kind", default="wave", choices=["wave", "elastic"])
     args = ap.parse_args()
     if args.cpu_table:
         cpu_table(args)
     elif args.profile_case:
         ne = tuple(int(v) for v in args.profile_case.split(","))
-        profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4, args.profile_batch, args.profile_tune)
+        profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4, args.profile_batch, args.profile_tune,
+                     args.profile_kind)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -969,8 +969,8 @@ int elastic_block_solve(ads_sim *s, int kind, int i, const T *main_in, T *out, c
     r.img = (const T *)ts.elimg[kind][i];
     r.img_bytes = ts.elimg_bytes[kind][i];
     r.c2 = T(-1);
-    r.ty = s->ty_el[pi];
     r.pair = 0;
+    r.ty = s->ty_el[pi];
     r.direct = 0;
     // body force of component i at level n: tau^2/rho r(t_n) dir_i g
     r.src.amp = s->tau * s->tau / s->rho * s->src.shape.dir[i];

@@ -491,7 +491,7 @@ size_t rhs_smem_bytes(int p, int elem, const Dims &d, int ty, int Sx, int Sy, in
     size_t n = (size_t)planes * q.rows * q.RS + 2 * (size_t)q.Smax * p * q.cld;
     size_t img = rhs_image_elems(p, d, Sx, Sy, seg);
     if (planes == 3) img += (size_t)Sx * seg * (2 * p + 1);   // Bx
-    return n * elem + 16 + ((img * elem + 15) & ~(size_t)15);
+    return n * elem + 32 + ((img * elem + 15) & ~(size_t)15);   // alignment of the carry buffers and tables
 }
 
 namespace {

@@ -89,66 +89,85 @@ __device__ __forceinline__ LineSm<T> line_carve(T *base, int m, int S)
 // The recurrences below subtract the oldest neighbour first and the newest
 // (v[k-1], resp. v[k+1]) last, so only one FMA per row sits on the chain
 // that runs through the segment; everything else overlaps it.
-template <typename T, int P, int SEG>
-__device__ __forceinline__ void seg_pass1(const T *fb, T (&v)[SEG])
+// Value type V of the line values: T (one line per thread), or float2 for
+// FP32 lines handled in pairs (two lines of the same 1D operator share every
+// coefficient load, and one packed FFMA2 does both lines' multiply-add).
+// c + a v and v a with a coefficient a of the 1D tables:
+__device__ __forceinline__ float madd(float a, float v, float c) { return fmaf(a, v, c); }
+__device__ __forceinline__ double madd(double a, double v, double c) { return fma(a, v, c); }
+__device__ __forceinline__ float2 madd(float a, float2 v, float2 c) { return __ffma2_rn(make_float2(a, a), v, c); }
+__device__ __forceinline__ float mulc(float v, float a) { return v * a; }
+__device__ __forceinline__ double mulc(double v, double a) { return v * a; }
+__device__ __forceinline__ float2 mulc(float2 v, float a) { return __fmul2_rn(v, make_float2(a, a)); }
+template <typename V>
+__device__ __forceinline__ V vzero();
+template <>
+__device__ __forceinline__ float vzero<float>() { return 0.0f; }
+template <>
+__device__ __forceinline__ double vzero<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.0f, 0.0f); }
+
+template <typename T, int P, int SEG, typename V = T>
+__device__ __forceinline__ void seg_pass1(const T *fb, V (&v)[SEG])
 {
     constexpr int W = 2 * P + 1;
 #pragma unroll
     for (int k = 0; k < SEG; ++k) {
-        T w = v[k];
+        V w = v[k];
 #pragma unroll
         for (int q = P; q >= 1; --q)
-            if (k - q >= 0) w -= fb[k * W + P - q] * v[k - q];
+            if (k - q >= 0) w = madd(-fb[k * W + P - q], v[k - q], w);
         v[k] = w;
     }
 }
 
-template <typename T, int P, int SEG>
-__device__ __forceinline__ void seg_pass2(const T *fb, const T *pb, const T (&c)[P], T (&v)[SEG])
+template <typename T, int P, int SEG, typename V = T>
+__device__ __forceinline__ void seg_pass2(const T *fb, const T *pb, const V (&c)[P], V (&v)[SEG])
 {
     constexpr int W = 2 * P + 1;
     // forward correction first: independent per row, off the chain
 #pragma unroll
     for (int k = 0; k < SEG; ++k) {
-        T w = v[k];
+        V w = v[k];
 #pragma unroll
-        for (int q = 0; q < P; ++q) w += c[q] * pb[k * P + q];
+        for (int q = 0; q < P; ++q) w = madd(pb[k * P + q], c[q], w);
         v[k] = w;
     }
 #pragma unroll
     for (int k = SEG - 1; k >= 0; --k) {
-        T w = v[k];
+        V w = v[k];
 #pragma unroll
         for (int q = P; q >= 1; --q)
-            if (k + q < SEG) w -= fb[k * W + P + q] * v[k + q];
-        v[k] = w * fb[k * W + P];
+            if (k + q < SEG) w = madd(-fb[k * W + P + q], v[k + q], w);
+        v[k] = mulc(w, fb[k * W + P]);
     }
 }
 
-template <typename T, int P, int SEG>
-__device__ __forceinline__ void seg_pass3(const T *qb, const T (&e)[P], T (&v)[SEG])
+template <typename T, int P, int SEG, typename V = T>
+__device__ __forceinline__ void seg_pass3(const T *qb, const V (&e)[P], V (&v)[SEG])
 {
 #pragma unroll
     for (int k = 0; k < SEG; ++k) {
-        T x = v[k];
+        V x = v[k];
 #pragma unroll
-        for (int q = 0; q < P; ++q) x += e[q] * qb[k * P + q];
+        for (int q = 0; q < P; ++q) x = madd(qb[k * P + q], e[q], x);
         v[k] = x;
     }
 }
 
-template <typename T, int P>
-__device__ __forceinline__ void carry_fwd(const T *Phi, int s, const T *CT, int ld, int j, T (&c)[P])
+template <typename T, int P, typename V = T>
+__device__ __forceinline__ void carry_fwd(const T *Phi, int s, const V *CT, int ld, int j, V (&c)[P])
 {
 #pragma unroll
-    for (int k = 0; k < P; ++k) c[k] = T(0);
+    for (int k = 0; k < P; ++k) c[k] = vzero<V>();
     for (int q = 0; q < s; ++q) {
-        T n[P];
+        V n[P];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
-            T acc = CT[(q * P + k) * ld + j];
+            V acc = CT[(q * P + k) * ld + j];
 #pragma unroll
-            for (int r = 0; r < P; ++r) acc += Phi[(q * P + k) * P + r] * c[r];
+            for (int r = 0; r < P; ++r) acc = madd(Phi[(q * P + k) * P + r], c[r], acc);
             n[k] = acc;
         }
 #pragma unroll
@@ -156,18 +175,18 @@ __device__ __forceinline__ void carry_fwd(const T *Phi, int s, const T *CT, int 
     }
 }
 
-template <typename T, int P>
-__device__ __forceinline__ void carry_bwd(const T *Psi, int S, int s, const T *CH, int ld, int j, T (&e)[P])
+template <typename T, int P, typename V = T>
+__device__ __forceinline__ void carry_bwd(const T *Psi, int S, int s, const V *CH, int ld, int j, V (&e)[P])
 {
 #pragma unroll
-    for (int k = 0; k < P; ++k) e[k] = T(0);
+    for (int k = 0; k < P; ++k) e[k] = vzero<V>();
     for (int q = S - 1; q > s; --q) {
-        T n[P];
+        V n[P];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
-            T acc = CH[(q * P + k) * ld + j];
+            V acc = CH[(q * P + k) * ld + j];
 #pragma unroll
-            for (int r = 0; r < P; ++r) acc += Psi[(q * P + k) * P + r] * e[r];
+            for (int r = 0; r < P; ++r) acc = madd(Psi[(q * P + k) * P + r], e[r], acc);
             n[k] = acc;
         }
 #pragma unroll
@@ -187,9 +206,9 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
 // registers.  Every thread of the synchronising group calls it (barrier id
 // 0: the whole block; else the named barrier of one line group); `on` marks
 // threads that own a segment.  CT/CH: [S][P][ld], slot j.
-template <typename T, int P, int SEG>
-__device__ __forceinline__ void seg_finish(const LineSm<T> &L, bool on, int s, int j, int ld, T *CT, T *CH,
-                                           T (&v)[SEG], int bar_id = 0, int bar_threads = 0)
+template <typename T, int P, int SEG, typename V = T>
+__device__ __forceinline__ void seg_finish(const LineSm<T> &L, bool on, int s, int j, int ld, V *CT, V *CH,
+                                           V (&v)[SEG], int bar_id = 0, int bar_threads = 0)
 {
     constexpr int W = 2 * P + 1;
     const int b0 = s * SEG;
@@ -199,17 +218,17 @@ __device__ __forceinline__ void seg_finish(const LineSm<T> &L, bool on, int s, i
     }
     group_sync(bar_id, bar_threads);
     if (on) {
-        T c[P];
-        carry_fwd<T, P>(L.Phi, s, CT, ld, j, c);
-        seg_pass2<T, P, SEG>(L.fac + b0 * W, L.phi + b0 * P, c, v);
+        V c[P];
+        carry_fwd<T, P, V>(L.Phi, s, CT, ld, j, c);
+        seg_pass2<T, P, SEG, V>(L.fac + b0 * W, L.phi + b0 * P, c, v);
 #pragma unroll
         for (int k = 0; k < P; ++k) CH[(s * P + k) * ld + j] = v[k];
     }
     group_sync(bar_id, bar_threads);
     if (on) {
-        T e[P];
-        carry_bwd<T, P>(L.Psi, L.S, s, CH, ld, j, e);
-        seg_pass3<T, P, SEG>(L.psi + b0 * P, e, v);
+        V e[P];
+        carry_bwd<T, P, V>(L.Psi, L.S, s, CH, ld, j, e);
+        seg_pass3<T, P, SEG, V>(L.psi + b0 * P, e, v);
     }
 }
 
@@ -424,7 +443,7 @@ __device__ __forceinline__ void phase1_extra(const T *colx, const long long (&zo
 enum { kSegMiddle = 0, kSegFirst = 1, kSegLast = 2, kSegGeneral = 3 };
 constexpr int kHeadRows = 8;   // leading rows of the first segment read from the band table (>= Toeplitz lo)
 
-template <typename T, int P, int SEG, int MODE>
+template <typename T, int P, int SEG, int MODE, bool PASS1 = true>
 __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx, int b0, const T (&mxm)[2 * P + 1],
                                            const T (&mxk)[2 * P + 1], const T *bMx, const T *bKx, int xlo, int xhi,
                                            const T *fb, const T *fx, T rowF, T c2, T (&v)[SEG])
@@ -469,7 +488,7 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
         const bool fin = MODE == kSegMiddle || MODE == kSegFirst || x < mx;
         v[k] = (fxb && fin ? rowF * fxb[k] : T(0)) - c2 * (acc1 + acc2);
     }
-    seg_pass1<T, P, SEG>(fb, v);   // rows are independent above; the chain is here
+    if (PASS1) seg_pass1<T, P, SEG>(fb, v);   // rows are independent above; the chain is here
 }
 
 // Phase 2 of the elastic K1, pass 1 for one row segment: form
@@ -477,7 +496,7 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
 // with a window of 2p+1 positions per plane that slides along the segment
 // (the band rows of every position from the table), then the local forward
 // substitution.  Rows past the line end meet zero band rows and F = 0.
-template <typename T, int P, int SEG, bool HAS3>
+template <typename T, int P, int SEG, bool HAS3, bool PASS1 = true>
 __device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, const T *row3, int mx, int b0,
                                               const T *bX1, const T *bX2, const T *bX3, const T *fb, const T *fx,
                                               T rowF, T c2, T cx, T (&v)[SEG])
@@ -509,7 +528,7 @@ __device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, cons
         }
         v[k] = (fx && x < mx ? rowF * fx[x] : T(0)) - c2 * (cx * acc1 + (acc2 + acc3));
     }
-    seg_pass1<T, P, SEG>(fb, v);
+    if (PASS1) seg_pass1<T, P, SEG>(fb, v);
 }
 
 // ---------------------------------------------------------------- K1
@@ -523,8 +542,10 @@ __device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, cons
 //  2. x-direction, thread per (row, segment of SEG): R = F - c2 (Kx s1 + Mx s2)
 //     is formed in registers while the local forward pass runs, then the
 //     carry exchange and passes 2-3; the row is written back to S1.
-//  3. whole plane in the tile: y-direction solve, thread per (x, segment),
-//     results stored from registers to global memory.
+//  3. whole plane in the tile: y-direction solve, thread per (x, segment)
+//     (FP32 single-CTA layout: per pair of columns x, x + mx/2 and segment,
+//     with packed FP32 instructions), results stored from registers to
+//     global memory.
 //  4. row tiles only: coalesced store of S1.
 // K1 CTA layouts: one CTA per tile, the 2-CTA cluster pair (FP32), or the
 // wide FP64 CTA for lines of more than 8 segments (every segment of a line
@@ -597,7 +618,9 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
     T *S2 = S1 + (size_t)q.rows * RS;
     T *S3 = S2 + (size_t)q.rows * RS;   // elastic K1 with a B plane only
     const int Smax = q.Smax;
-    T *CT = S3 + ((EL && el->s3) ? (size_t)q.rows * RS : 0);
+    // carry buffers 8-byte aligned (the y sweep of line pairs keeps float2 carries)
+    T *CT = reinterpret_cast<T *>(
+        (reinterpret_cast<uintptr_t>(S3 + ((EL && el->s3) ? (size_t)q.rows * RS : 0)) + 7) & ~(uintptr_t)7);
     T *CH = CT + (size_t)Smax * P * cld;
     // the 1D tables arrive as one bulk copy into a 16-byte aligned region
     T *tb = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(CH + (size_t)Smax * P * cld) + 15) & ~(uintptr_t)15);
@@ -772,11 +795,11 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
             const bool regular = LX.S >= 2 && xlo <= kHeadRows && xhi >= (LX.S - 1) * SEG && mx >= (LX.S - 1) * SEG + P;
             if constexpr (EL) {
                 if (el->s3)
-                    phase2_fwd_el<T, P, SEG, true>(row1, row2, S3 + (size_t)l * RS, mx, b0, bKx, bMx, bBx, fb, srcF,
-                                                   rowF, c2, el->cx, v);
+                    phase2_fwd_el<T, P, SEG, true>(row1, row2, S3 + (size_t)l * RS, mx, b0, bKx, bMx, bBx, fb,
+                                                       srcF, rowF, c2, el->cx, v);
                 else
-                    phase2_fwd_el<T, P, SEG, false>(row1, row2, nullptr, mx, b0, bKx, bMx, bBx, fb, srcF, rowF, c2,
-                                                    el->cx, v);
+                    phase2_fwd_el<T, P, SEG, false>(row1, row2, nullptr, mx, b0, bKx, bMx, bBx, fb, srcF, rowF,
+                                                        c2, el->cx, v);
             } else if (regular && s > 0 && s < LX.S - 1)
                 phase2_fwd<T, P, SEG, kSegMiddle>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
             else if (regular && s == 0)
@@ -814,7 +837,46 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
             c1 = half ? mx : q.xcut;
         }
         const int ycut = PAIR ? q.ycut : my;
-        const int CG = (c1 - c0 + 31) >> 5;
+        // FP32 single-CTA layout: the y sweep runs on line pairs (one packed
+        // instruction for two columns; 8-11 % faster K1 than a line per thread)
+        constexpr bool Y2 = sizeof(T) == 4 && !PAIR;
+        if constexpr (Y2) {
+            // line pairs: thread xl holds columns x0 = c0 + xl and x0 + H (H =
+            // half the columns, rounded up), both solved by the same packed
+            // instructions; slot xl of the carry buffers holds the pair
+            const int ncol = c1 - c0, H = (ncol + 1) >> 1;
+            const int CG = (H + 31) >> 5;
+            const int gpr3 = min(nwarps / LY.S, 15);
+            float2 *CT2 = reinterpret_cast<float2 *>(CT), *CH2 = reinterpret_cast<float2 *>(CH);
+            for (int g0 = 0; g0 < CG; g0 += gpr3) {
+                const int gi = warp / LY.S, s = warp % LY.S;
+                if (gi >= gpr3 || g0 + gi >= CG) continue;   // the whole column group skips alike
+                const int xl = (g0 + gi) * 32 + lane;
+                const bool on = xl < H, on1 = xl + H < ncol;
+                const int x0 = c0 + xl;
+                const int b0 = s * SEG;
+                const int n = on ? min(SEG, my - b0) : 0;
+                float2 v[SEG];
+#pragma unroll
+                for (int k = 0; k < SEG; ++k) {
+                    const T *row = S1 + (size_t)(b0 + k) * RS + x0;
+                    v[k] = (k < n) ? make_float2(row[0], on1 ? row[H] : 0.0f) : make_float2(0.0f, 0.0f);
+                }
+                if (on) seg_pass1<T, P, SEG, float2>(LY.fac + b0 * W, v);
+                seg_finish<T, P, SEG, float2>(LY, on, s, xl, cld >> 1, CT2, CH2, v, 1 + gi, 32 * LY.S);
+                if (on) {
+                    T *dst = a.out + (long long)z * plane + (long long)b0 * sx + x0;
+#pragma unroll
+                    for (int k = 0; k < SEG; ++k) {
+                        if (k < n) {
+                            dst[(long long)k * sx] = v[k].x;
+                            if (on1) dst[(long long)k * sx + H] = v[k].y;
+                        }
+                    }
+                }
+            }
+        }
+        const int CG = Y2 ? 0 : (c1 - c0 + 31) >> 5;
         const int gpr3 = min(nwarps / LY.S, 15);
         for (int g0 = 0; g0 < CG; g0 += gpr3) {
             const int gi = warp / LY.S, s = warp % LY.S;
@@ -1154,12 +1216,14 @@ cudaError_t rhs_seg_p(const RhsArgs<T> *a, int n, cudaStream_t s)
 }
 
 // one elastic K1 launch: single-CTA layout (wide for FP64 lines of more than
-// 8 segments), never a cluster pair, never direct mode
+// 8 segments); never a cluster pair (measured slower at 96^3), never direct mode
 template <typename T, int P, int SEG, int LAYOUT>
 cudaError_t rhs_el_p(const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
 {
-    if (!rhs_entry_ok(a, SEG) || a.pair || a.direct || el.n < 0 || el.n > kMaxExtra) return cudaErrorInvalidValue;
-    if (std::max(a.lx.S, a.ty == a.d.my ? a.ly.S : 0) > RhsThreads<T, LAYOUT>::value / 32)
+    constexpr bool PAIR = LAYOUT == kLayoutPair;
+    if (!rhs_entry_ok(a, SEG) || (a.pair != 0) != PAIR || a.direct || el.n < 0 || el.n > kMaxExtra)
+        return cudaErrorInvalidValue;
+    if (std::max(a.lx.S, (PAIR || a.ty == a.d.my) ? a.ly.S : 0) > RhsThreads<T, LAYOUT>::value / 32)
         return cudaErrorInvalidValue;   // a segment without a warp
     for (int t = 0; t < el.n; ++t)
         if (!el.ex[t].in || !el.ex[t].by || !el.ex[t].bz || (el.ex[t].slot != 2 && el.ex[t].slot != 3) ||
@@ -1170,9 +1234,9 @@ cudaError_t rhs_el_p(const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
     g.a = a;
     g.el = el;
     // planes, carry buffers and the table image as the kernel carves them
-    const RhsPlan q = rhs_plan(a.d.mx, a.d.my, a.ty, 0, a.lx.S, a.ly.S);
+    const RhsPlan q = rhs_plan(a.d.mx, a.d.my, a.ty, PAIR ? 1 : 0, a.lx.S, a.ly.S);
     const size_t n = (size_t)(el.s3 ? 3 : 2) * q.rows * q.RS + 2 * (size_t)q.Smax * P * q.cld;
-    const size_t smem = n * sizeof(T) + 16 + (((size_t)a.img_bytes + 15) & ~(size_t)15);
+    const size_t smem = n * sizeof(T) + 32 + (((size_t)a.img_bytes + 15) & ~(size_t)15);
     static std::atomic<size_t> smem_set{48 * 1024};
     if (cudaError_t e = raise_dyn_smem(k_rhs_el<T, P, SEG, LAYOUT>, smem_set, smem); e != cudaSuccess) return e;
     ++g_launches;
@@ -1182,12 +1246,16 @@ cudaError_t rhs_el_p(const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
     cfg.blockDim = dim3(RhsThreads<T, LAYOUT>::value, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     std::memset(attr, 0, sizeof(attr));
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;   // pairs: the two halves of one z-plane
+    attr[1].val.clusterDim.x = 2;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = PAIR ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, k_rhs_el<T, P, SEG, LAYOUT>, g);
 }
 
@@ -1196,8 +1264,10 @@ cudaError_t rhs_el_layout(const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_
 {
     const int layout = rhs_layout(a);
     if (layout == kLayoutSingle) return rhs_el_p<T, P, SEG, kLayoutSingle>(a, el, s);
-    if constexpr (sizeof(T) == 8 && SEG != kSegLong) {
-        if (layout == kLayoutWide) return rhs_el_p<T, P, SEG, kLayoutWide>(a, el, s);
+    if constexpr (SEG != kSegLong) {
+        if constexpr (sizeof(T) == 8) {
+            if (layout == kLayoutWide) return rhs_el_p<T, P, SEG, kLayoutWide>(a, el, s);
+        }
     }
     return cudaErrorInvalidValue;
 }
