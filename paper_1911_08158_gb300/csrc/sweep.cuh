@@ -443,7 +443,7 @@ __device__ __forceinline__ void phase1_extra(const T *colx, const long long (&zo
 enum { kSegMiddle = 0, kSegFirst = 1, kSegLast = 2, kSegGeneral = 3 };
 constexpr int kHeadRows = 8;   // leading rows of the first segment read from the band table (>= Toeplitz lo)
 
-template <typename T, int P, int SEG, int MODE, bool PASS1 = true>
+template <typename T, int P, int SEG, int MODE>
 __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx, int b0, const T (&mxm)[2 * P + 1],
                                            const T (&mxk)[2 * P + 1], const T *bMx, const T *bKx, int xlo, int xhi,
                                            const T *fb, const T *fx, T rowF, T c2, T (&v)[SEG])
@@ -488,7 +488,7 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
         const bool fin = MODE == kSegMiddle || MODE == kSegFirst || x < mx;
         v[k] = (fxb && fin ? rowF * fxb[k] : T(0)) - c2 * (acc1 + acc2);
     }
-    if (PASS1) seg_pass1<T, P, SEG>(fb, v);   // rows are independent above; the chain is here
+    seg_pass1<T, P, SEG>(fb, v);   // rows are independent above; the chain is here
 }
 
 // Phase 2 of the elastic K1, pass 1 for one row segment: form
@@ -496,7 +496,7 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
 // with a window of 2p+1 positions per plane that slides along the segment
 // (the band rows of every position from the table), then the local forward
 // substitution.  Rows past the line end meet zero band rows and F = 0.
-template <typename T, int P, int SEG, bool HAS3, bool PASS1 = true>
+template <typename T, int P, int SEG, bool HAS3>
 __device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, const T *row3, int mx, int b0,
                                               const T *bX1, const T *bX2, const T *bX3, const T *fb, const T *fx,
                                               T rowF, T c2, T cx, T (&v)[SEG])
@@ -528,7 +528,7 @@ __device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, cons
         }
         v[k] = (fx && x < mx ? rowF * fx[x] : T(0)) - c2 * (cx * acc1 + (acc2 + acc3));
     }
-    if (PASS1) seg_pass1<T, P, SEG>(fb, v);
+    seg_pass1<T, P, SEG>(fb, v);
 }
 
 // ---------------------------------------------------------------- K1
