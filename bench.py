@@ -421,6 +421,7 @@ def run_batch(args, stream, flush):
     torch.cuda.synchronize()
     reps = max(1, min(args.steps, 5))
     t = 0.0
+    l0 = ads.launch_count()
     for _ in range(reps):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -430,6 +431,7 @@ def run_batch(args, stream, flush):
         e1.record(stream)
         e1.synchronize()
         t += e0.elapsed_time(e1) / 1e3
+    launches_per_step = (ads.launch_count() - l0) / (reps * 50)
     n = sum(dofs(s) for s in sims)
     interior = sum((s.n[0] - 2) * (s.n[1] - 2) * (s.n[2] - 2) for s in sims)
     # kernel shares: each member's kernels timed by CUDA events in one profiled
@@ -469,7 +471,7 @@ def run_batch(args, stream, flush):
     return {"value": dof_steps * reps / t, "unit": UNIT, "simulations": len(cases), "steps_each": 50,
             "total_dofs": n, "interior_dofs": interior, "reps": reps, "ms_per_rep": t / reps * 1e3,
             "tiles_fused": sum(1 for s, r in zip(cases, tiles) if r == s.n_elem[1] + s.p - 2),
-            "roofline": roof,
+            "launches_per_step": launches_per_step, "roofline": roof,
             "workload": "batch64_pwave_uneven_32to160_p2p3_50steps_fp32"}
 
 
@@ -710,6 +712,22 @@ def profile_case(ne, p: int, steps: int, batch: int = 1, tune: int = 3, kind: st
     from paper_1911_08158_gb300 import workloads as wl
 
     torch.cuda.set_device(0)
+    if kind == "batch64":
+        # the 64-simulation batch (1.1 GB): 2 warm-up grouped steps, then `steps`
+        cases = wl.batch_cases(count=64, seed=0, steps=50)
+        sims = []
+        for c in cases:
+            sim = ads.Simulation(c.n_elem, c.p, c.tau, precision="fp32")
+            sim.set_gaussian_state(c.u0, None)
+            sim.autotune(tune)
+            sims.append(sim)
+        ads.batch_step(sims, 2)
+        for _ in range(steps):
+            ads.batch_step(sims, 1)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "batch64", "steps": steps, "tune": tune,
+                          "device_bytes": sum(s.device_bytes for s in sims)}))
+        return
     if kind == "elastic":
         c = wl.elastic_case(ne=ne, p=p)
         sim = ads.Simulation(c.n_elem, c.p, c.tau, kind="elastic", lam=c.lam, mu=c.mu, rho=c.rho, precision="fp32")
@@ -760,12 +778,12 @@ def main():
     ap.add_argument("--profile-p", type=int, default=2)
     ap.add_argument("--profile-batch", type=int, default=1, help="simulations advanced together in the profile case")
     ap.add_argument("--profile-tune", type=int, default=3, help="autotuner trial steps in the profile case")
-    ap.add_argument("--profile-kind", default="wave", choices=["wave", "elastic"])
+    ap.add_argument("--profile-kind", default="wave", choices=["wave", "elastic", "batch64"])
     args = ap.parse_args()
     if args.cpu_table:
         cpu_table(args)
     elif args.profile_case:
-        ne = tuple(int(v) for v in args.profile_case.split(","))
+        ne = tuple(int(v) for v in args.profile_case.split(",")) if args.profile_kind != "batch64" else (0,)
         profile_case(ne[0] if len(ne) == 1 else ne, args.profile_p, 4, args.profile_batch, args.profile_tune,
                      args.profile_kind)
     elif args.impl == "reference":

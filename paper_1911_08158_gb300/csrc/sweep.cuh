@@ -279,7 +279,8 @@ constexpr int kPhase1Lookahead = 1;   // stream rows whose loads are in flight a
 // offset of plane clamp(z-P+k) (uniform over the CTA).
 // SC (the elastic K1): s2 = cy (Ky t1) + cz (My t2), the two contractions
 // scaled after they are formed.
-template <typename T, int P, bool INTERIOR, bool SC = false, int PF = kPhase1Lookahead>
+// MASS (the elastic K1's upper blocks, cy = cz = 0): only s1 = My Mz p; s2 = 0.
+template <typename T, int P, bool INTERIOR, bool SC = false, bool MASS = false, int PF = kPhase1Lookahead>
 __device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zoff)[2 * P + 1], int sx, int my,
                                              const T (&cm)[2 * P + 1], const T (&ck)[2 * P + 1],
                                              const T (&mym)[2 * P + 1], const T (&myk)[2 * P + 1], const T *bMy,
@@ -322,7 +323,7 @@ __device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zo
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 t1 = fma2(cm[k], v[k], t1);
-                t2 = fma2(ck[k], v[k], t2);
+                if (!MASS) t2 = fma2(ck[k], v[k], t2);
             }
             r1[j] = t1;
             r2[j] = t2;
@@ -342,6 +343,7 @@ __device__ __forceinline__ void phase1_chunk(const T *colx, const long long (&zo
                     // window row y-P+q = stream index r-2P+q  ->  ring slot (j-2P+q) mod W
                     const int sl = (j - 2 * P + q + 2 * W) % W;
                     a = fma2(bm[q], r1[sl], a);
+                    if (MASS) continue;
                     c = fma2(bk[q], r1[sl], c);
                     if (SC) c2 = fma2(bm[q], r2[sl], c2);
                     else c = fma2(bm[q], r2[sl], c);
@@ -496,10 +498,13 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
 // with a window of 2p+1 positions per plane that slides along the segment
 // (the band rows of every position from the table), then the local forward
 // substitution.  Rows past the line end meet zero band rows and F = 0.
-template <typename T, int P, int SEG, bool HAS3>
+// TOEP: the whole segment lies in the Toeplitz interior rows, whose band rows
+// x1m, x2m, x3m are held in registers (else every row is read from the table).
+template <typename T, int P, int SEG, bool HAS3, bool TOEP>
 __device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, const T *row3, int mx, int b0,
-                                              const T *bX1, const T *bX2, const T *bX3, const T *fb, const T *fx,
-                                              T rowF, T c2, T cx, T (&v)[SEG])
+                                              const T *bX1, const T *bX2, const T *bX3, const T (&x1m)[2 * P + 1],
+                                              const T (&x2m)[2 * P + 1], const T (&x3m)[2 * P + 1], const T *fb,
+                                              const T *fx, T rowF, T c2, T cx, T (&v)[SEG])
 {
     constexpr int W = 2 * P + 1;
     T w1[W], w2[W], w3[W];
@@ -522,9 +527,9 @@ __device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, cons
 #pragma unroll
         for (int q = 0; q < W; ++q) {
             const int sl = (k + q) % W;
-            acc1 += bX1[x * W + q] * w1[sl];
-            acc2 += bX2[x * W + q] * w2[sl];
-            if (HAS3) acc3 += bX3[x * W + q] * w3[sl];
+            acc1 += (TOEP ? x1m[q] : bX1[x * W + q]) * w1[sl];
+            acc2 += (TOEP ? x2m[q] : bX2[x * W + q]) * w2[sl];
+            if (HAS3) acc3 += (TOEP ? x3m[q] : bX3[x * W + q]) * w3[sl];
         }
         v[k] = (fx && x < mx ? rowF * fx[x] : T(0)) - c2 * (cx * acc1 + (acc2 + acc3));
     }
@@ -717,7 +722,14 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
             if (!live) continue;
             T *c1 = S1 + x - (size_t)y0 * RS, *c2 = S2 + x - (size_t)y0 * RS;
             if constexpr (EL) {
-                if (winter)
+                const bool mass = el->cy == T(0) && el->cz == T(0);   // uniform over the launch
+                if (mass && winter)
+                    phase1_chunk<T, P, true, true, true>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi,
+                                                         yb, ye, c1, c2, RS, el->cy, el->cz);
+                else if (mass)
+                    phase1_chunk<T, P, false, true, true>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi,
+                                                          yb, ye, c1, c2, RS, el->cy, el->cz);
+                else if (winter)
                     phase1_chunk<T, P, true, true>(a.in + x, zoff, sx, my, cm, ck, mym, myk, gMy, gKy, ylo, yhi, yb,
                                                    ye, c1, c2, RS, el->cy, el->cz);
                 else
@@ -794,12 +806,28 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
             // every row from the table (its rows past hi are not Toeplitz)
             const bool regular = LX.S >= 2 && xlo <= kHeadRows && xhi >= (LX.S - 1) * SEG && mx >= (LX.S - 1) * SEG + P;
             if constexpr (EL) {
-                if (el->s3)
-                    phase2_fwd_el<T, P, SEG, true>(row1, row2, S3 + (size_t)l * RS, mx, b0, bKx, bMx, bBx, fb,
-                                                       srcF, rowF, c2, el->cx, v);
+                T x1m[W], x2m[W], x3m[W];
+                const int mid = xlo < xhi ? xlo : 0;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    x1m[k] = bKx[mid * W + k];
+                    x2m[k] = bMx[mid * W + k];
+                    x3m[k] = el->s3 ? bBx[mid * W + k] : T(0);
+                }
+                const bool toep = b0 >= xlo && b0 + SEG <= xhi;   // uniform over the warp
+                const T *r3 = el->s3 ? S3 + (size_t)l * RS : nullptr;
+                if (el->s3 && toep)
+                    phase2_fwd_el<T, P, SEG, true, true>(row1, row2, r3, mx, b0, bKx, bMx, bBx, x1m, x2m, x3m, fb,
+                                                         srcF, rowF, c2, el->cx, v);
+                else if (el->s3)
+                    phase2_fwd_el<T, P, SEG, true, false>(row1, row2, r3, mx, b0, bKx, bMx, bBx, x1m, x2m, x3m, fb,
+                                                          srcF, rowF, c2, el->cx, v);
+                else if (toep)
+                    phase2_fwd_el<T, P, SEG, false, true>(row1, row2, r3, mx, b0, bKx, bMx, bBx, x1m, x2m, x3m, fb,
+                                                          srcF, rowF, c2, el->cx, v);
                 else
-                    phase2_fwd_el<T, P, SEG, false>(row1, row2, nullptr, mx, b0, bKx, bMx, bBx, fb, srcF, rowF,
-                                                        c2, el->cx, v);
+                    phase2_fwd_el<T, P, SEG, false, false>(row1, row2, r3, mx, b0, bKx, bMx, bBx, x1m, x2m, x3m, fb,
+                                                           srcF, rowF, c2, el->cx, v);
             } else if (regular && s > 0 && s < LX.S - 1)
                 phase2_fwd<T, P, SEG, kSegMiddle>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
             else if (regular && s == 0)
