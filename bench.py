@@ -13,7 +13,8 @@ step; inputs stay resident in HBM.
            both simulations advance together through ads_batch_step (one
            grouped launch per kernel and degree, the two degrees overlapping)
   e2e    : the same metric through the C ABI with pinned host buffers: per
-           step set_state(u, v, a) from host, 200 steps, get_state to host
+           step set_state(u, v, a) of both simulations from host, 200 steps of
+           both together (ads_batch_step), get_state of both to host
   fp64   : the FP64 path on the same workload (the path the FP32 one beats)
   roofline: dominant kernel, algorithmic bytes / its CUDA-event time
   cpu_baseline: the FP64 CPU oracle on a bounded sample of the workload
@@ -352,7 +353,9 @@ def run_ours(args):
         for s, bufs in zip(sims, host):
             ptr = [b.data_ptr() for b in bufs]
             ads.ads._check(lib.ads_set_state(s.handle, ptr[0], ptr[1], ptr[2], s.count, ads.ADS_HOST))
-            s.step(NSTEPS)
+        ads.batch_step(sims, NSTEPS)   # both simulations together, as in the device-timed line
+        for s, bufs in zip(sims, host):
+            ptr = [b.data_ptr() for b in bufs]
             ads.ads._check(lib.ads_get_state(s.handle, ptr[0], ptr[1], ptr[2], s.count, ads.ADS_HOST))
     torch.cuda.synchronize()
     te = time.perf_counter() - t0

@@ -567,8 +567,7 @@ int stage_out(ads_sim *s, Scratch &sc, const double *interior, double *dst, int 
     if (mem == ADS_HOST) {
         ADS_CK(cudaMemcpyAsync(dst, full, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     }
-    ADS_CK(cudaStreamSynchronize(s->stream));
-    return ADS_OK;
+    return ADS_OK;   // the caller waits for the stream once, after its last field
 }
 
 // A bounded wait that gave up records a nonzero word; report it once.
@@ -1875,6 +1874,7 @@ int ads_get_state(ads_sim_t *s, double *u, double *v, double *a, size_t count, i
         for (int c = 0; c < comps; ++c)
             if ((rc = stage_out(s, sc, ins[f] + (size_t)c * cnt, outs[f] + c * ncomp, mem, ncomp))) return rc;
     }
+    ADS_CK(cudaStreamSynchronize(s->stream));
     return check_device_error(s);
 }
 
@@ -2034,7 +2034,9 @@ int ads_apply(ads_sim_t *s, int op, const double *in, double *out, size_t count,
     default: return fail(ADS_ERR_INVALID_ARG, "ads_apply: unknown op");
     }
     if (rc) return rc;
-    return stage_out(s, sc, y, out, mem, count);
+    if ((rc = stage_out(s, sc, y, out, mem, count))) return rc;
+    ADS_CK(cudaStreamSynchronize(s->stream));
+    return ADS_OK;
 }
 
 // raw state arrays of the simulation: scalar wave p, q, a; elasticity U^n, U^{n-1}
