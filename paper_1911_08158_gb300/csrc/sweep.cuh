@@ -548,9 +548,9 @@ __device__ __forceinline__ void phase2_fwd_el(const T *row1, const T *row2, cons
 //     is formed in registers while the local forward pass runs, then the
 //     carry exchange and passes 2-3; the row is written back to S1.
 //  3. whole plane in the tile: y-direction solve, thread per (x, segment)
-//     (FP32 single-CTA layout: per pair of columns x, x + mx/2 and segment,
-//     with packed FP32 instructions), results stored from registers to
-//     global memory.
+//     (FP32: per pair of columns x, x + H and segment, H half the CTA's
+//     columns, with packed FP32 instructions), results stored from registers
+//     to global memory.
 //  4. row tiles only: coalesced store of S1.
 // K1 CTA layouts: one CTA per tile, the 2-CTA cluster pair (FP32), or the
 // wide FP64 CTA for lines of more than 8 segments (every segment of a line
@@ -865,9 +865,9 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
             c1 = half ? mx : q.xcut;
         }
         const int ycut = PAIR ? q.ycut : my;
-        // FP32 single-CTA layout: the y sweep runs on line pairs (one packed
-        // instruction for two columns; 8-11 % faster K1 than a line per thread)
-        constexpr bool Y2 = sizeof(T) == 4 && !PAIR;
+        // FP32: the y sweep runs on line pairs (one packed instruction for two
+        // columns; 8-11 % faster K1 than a line per thread)
+        constexpr bool Y2 = sizeof(T) == 4;
         if constexpr (Y2) {
             // line pairs: thread xl holds columns x0 = c0 + xl and x0 + H (H =
             // half the columns, rounded up), both solved by the same packed
@@ -887,7 +887,10 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
                 float2 v[SEG];
 #pragma unroll
                 for (int k = 0; k < SEG; ++k) {
-                    const T *row = S1 + (size_t)(b0 + k) * RS + x0;
+                    const int r = b0 + k;   // a pair's rows below ycut live in rank 0's S1
+                    const T *row =
+                        (PAIR ? (r < ycut ? Slo + (size_t)r * RS : Shi + (size_t)(r - ycut) * RS) : S1 + (size_t)r * RS) +
+                        x0;
                     v[k] = (k < n) ? make_float2(row[0], on1 ? row[H] : 0.0f) : make_float2(0.0f, 0.0f);
                 }
                 if (on) seg_pass1<T, P, SEG, float2>(LY.fac + b0 * W, v);

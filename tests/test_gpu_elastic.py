@@ -87,3 +87,16 @@ def test_96cubed_elasticity_100_steps():
         for n in (10, 100):
             _check(got[n], ref[n], precision, case.tau, n, "%s step %d" % (precision, n))
             print("96^3 elasticity %s rel-L2 U at %d: %.3e" % (precision, n, rel_l2(got[n][0], ref[n][0])))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("ne", [(65, 14, 9), (129, 129, 4)])
+def test_segment_lengths(ne, precision):
+    """Grids whose lines take 33-row segments (65 unknowns along x) and, in
+    FP32, 44-row segments (129 x 129 planes, which the elastic K1 also splits
+    into row tiles because three such planes exceed shared memory) in the
+    fused elastic step, against the oracle."""
+    case = wl.elastic_case(ne=ne, p=2, tau=3e-3, steps=6, seed=7, sigma=0.1)
+    ref = oracle_elastic(case, 6)[6]
+    _, got = gpu_elastic(case, 6, precision)
+    _check(got[6], ref, precision, case.tau, 6, "%s %s" % (precision, ne))
