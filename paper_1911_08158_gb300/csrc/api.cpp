@@ -1254,14 +1254,18 @@ int batch_graph(BatchRes &br, const std::vector<ads_sim *> &g, cudaStream_t st, 
     return ADS_OK;
 }
 
-// Advance every group by nsteps: each group runs on its own stream after
-// the members' streams (pending work on any member) and the members'
-// streams wait for it again, so stream order per simulation is kept.
-int batch_groups(std::map<std::pair<int, int>, std::vector<ads_sim *>> &groups, int nsteps)
+// Advance every group by nsteps, and the other simulations (elasticity, the
+// residual-corrected FP32 step) by ads_step on their own streams.  Each group
+// runs on its own stream after the members' streams (pending work on any
+// member) and the members' streams wait for it again, so stream order per
+// simulation is kept.  Every group joins the members' streams before any
+// group's completion is queued on them: members that share one stream
+// (the usual case) would otherwise make each group wait for the one before,
+// and the groups would run one after another instead of side by side.
+int batch_groups(std::map<std::pair<int, int>, std::vector<ads_sim *>> &groups, const std::vector<ads_sim *> &others,
+                 int nsteps)
 {
-    if (groups.empty()) return ADS_OK;
-    std::lock_guard<std::mutex> lock(batch_mutex());
-    BatchRes &br = batch_res(groups.begin()->second[0]->device);
+    std::unique_lock<std::mutex> lock(batch_mutex());
     std::vector<cudaEvent_t> evs;
     auto new_event = [&](cudaEvent_t *e) -> int {
         ADS_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
@@ -1276,42 +1280,62 @@ int batch_groups(std::map<std::pair<int, int>, std::vector<ads_sim *>> &groups, 
         }
     } cleanup{evs};
     int rc;
-    for (auto &kv : groups) {
-        std::vector<ads_sim *> &g = kv.second;
+    struct Run {
+        std::vector<ads_sim *> *g;
         cudaStream_t st;
-        if ((rc = group_stream(br, kv.first.first, kv.first.second, &st))) return rc;
         std::vector<cudaStream_t> member_streams;
-        for (ads_sim *s : g)
-            if (std::find(member_streams.begin(), member_streams.end(), s->stream) == member_streams.end())
-                member_streams.push_back(s->stream);
-        for (cudaStream_t ms : member_streams) {
+    };
+    std::vector<Run> runs;
+    // 1. every group's stream joins its members' streams
+    for (auto &kv : groups) {
+        Run r{&kv.second, nullptr, {}};
+        BatchRes &br = batch_res(kv.second[0]->device);
+        if ((rc = group_stream(br, kv.first.first, kv.first.second, &r.st))) return rc;
+        for (ads_sim *s : kv.second)
+            if (std::find(r.member_streams.begin(), r.member_streams.end(), s->stream) == r.member_streams.end())
+                r.member_streams.push_back(s->stream);
+        for (cudaStream_t ms : r.member_streams) {
             cudaEvent_t e;
             if ((rc = new_event(&e))) return rc;
             ADS_CK(cudaEventRecord(e, ms));
-            ADS_CK(cudaStreamWaitEvent(st, e, 0));
+            ADS_CK(cudaStreamWaitEvent(r.st, e, 0));
         }
+        runs.push_back(std::move(r));
+    }
+    // 2. the groups' steps
+    for (Run &r : runs) {
+        std::vector<ads_sim *> &g = *r.g;
+        BatchRes &br = batch_res(g[0]->device);
         int left = nsteps;
         bool warmed = true;
         for (ads_sim *s : g) warmed = warmed && s->warmed;
         if (!warmed) {   // first grouped step outside capture (kernel attributes)
-            if ((rc = group_steps(g, st, 1, left == 1))) return rc;
+            if ((rc = group_steps(g, r.st, 1, left == 1))) return rc;
             for (ads_sim *s : g) s->warmed = true;
             --left;
         }
         if (left >= kBatchChunk) {
             BatchGraph *bg;
-            if ((rc = batch_graph(br, g, st, &bg))) return rc;
+            if ((rc = batch_graph(br, g, r.st, &bg))) return rc;
             const int full = left / kBatchChunk;
-            for (int i = 0; i < full; ++i) ADS_CK(cudaGraphLaunch(bg->exec, st));
+            for (int i = 0; i < full; ++i) ADS_CK(cudaGraphLaunch(bg->exec, r.st));
             ads::g_launches += (unsigned long long)full * bg->launches;
             left -= full * kBatchChunk;
         }
-        if (left > 0 && (rc = group_steps(g, st, left, true))) return rc;
+        if (left > 0 && (rc = group_steps(g, r.st, left, true))) return rc;
         for (ads_sim *s : g) s->h_step += nsteps;
+    }
+    // 3. the other simulations, queued on their own streams after the joins
+    // above, so they run beside the groups (ads_step takes no batch lock)
+    lock.unlock();
+    for (ads_sim *s : others)
+        if ((rc = ads_step(s, nsteps))) return rc;
+    // 4. the members' streams wait for their groups
+    for (Run &r : runs) {
         cudaEvent_t done;
         if ((rc = new_event(&done))) return rc;
-        ADS_CK(cudaEventRecord(done, st));
-        for (cudaStream_t ms : member_streams) ADS_CK(cudaStreamWaitEvent(ms, done, 0));
+        ADS_CK(cudaEventRecord(done, r.st));
+        for (cudaStream_t ms : r.member_streams) ADS_CK(cudaStreamWaitEvent(ms, done, 0));
     }
     return ADS_OK;
 }
@@ -1928,16 +1952,13 @@ int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps)
     // elasticity (and the residual-corrected FP32 step) advances on each
     // simulation's own stream meanwhile
     std::map<std::pair<int, int>, std::vector<ads_sim *>> groups;
+    std::vector<ads_sim *> others;
     for (int i = 0; i < count; ++i) {
         ads_sim *s = sims[i];
-        if (s->kind == ADS_SCALAR_WAVE && !s->refine) {
-            groups[{s->prec, s->p}].push_back(s);
-        } else {
-            int rc = ads_step(s, nsteps);
-            if (rc) return rc;
-        }
+        if (s->kind == ADS_SCALAR_WAVE && !s->refine) groups[{s->prec, s->p}].push_back(s);
+        else others.push_back(s);
     }
-    return batch_groups(groups, nsteps);
+    return batch_groups(groups, others, nsteps);
 }
 
 int ads_selftest_timeout(int device, long long cycles)

@@ -1187,9 +1187,6 @@ cudaError_t rhs_group_p(const RhsArgs<T> *a, const int *order, int n, cudaStream
 }
 
 // A single simulation is a group of one: one instantiation per (T, P, SEG,
-// pairing) serves both (its parameters are read with a run-time index, which
-// keeps them out of the register budget of the sweeps).  Pairs are FP32 only.
-// A single simulation is a group of one: one instantiation per (T, P, SEG,
 // layout) serves both (its parameters are read with a run-time index, which
 // keeps them out of the register budget of the sweeps).  Pairs are FP32
 // only and need at most 8 segments per line; FP64 lines of more than 8
