@@ -442,8 +442,9 @@ __device__ __forceinline__ void phase1_extra(const T *colx, const long long (&zo
 // forward substitution on it.  FAST: a full segment inside the Toeplitz
 // range (no predicates, band rows in registers).
 // Segment kinds of the x-direction pass 1.
-enum { kSegMiddle = 0, kSegFirst = 1, kSegLast = 2, kSegGeneral = 3 };
+enum { kSegMiddle = 0, kSegFirst = 1, kSegLast = 2, kSegGeneral = 3, kSegLastAll = 4 };
 constexpr int kHeadRows = 8;   // leading rows of the first segment read from the band table (>= Toeplitz lo)
+constexpr int kTailRows = 8;   // trailing rows of the last segment read from the table (>= its rows from Toeplitz hi)
 
 template <typename T, int P, int SEG, int MODE>
 __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx, int b0, const T (&mxm)[2 * P + 1],
@@ -458,7 +459,7 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
         bool in_;
         if (MODE == kSegMiddle) in_ = true;
         else if (MODE == kSegFirst) in_ = j >= P;                  // x < 0 is outside
-        else if (MODE == kSegLast) in_ = xx < mx;                  // b0 - P >= 0 here
+        else if (MODE == kSegLast || MODE == kSegLastAll) in_ = xx < mx;   // b0 - P >= 0 here
         else in_ = xx >= 0 && xx < mx;
         a1[j] = in_ ? row1[xx] : T(0);
         a2[j] = in_ ? row2[xx] : T(0);
@@ -468,7 +469,8 @@ __device__ __forceinline__ void phase2_fwd(const T *row1, const T *row2, int mx,
     for (int k = 0; k < SEG; ++k) {
         const int x = b0 + k;
         T bm[W], bk[W];
-        const bool table = MODE == kSegLast || (MODE == kSegFirst && k < kHeadRows);
+        const bool table = MODE == kSegLastAll || (MODE == kSegLast && k >= SEG - kTailRows) ||
+                           (MODE == kSegFirst && k < kHeadRows);
         if (MODE == kSegGeneral) {
             band_row<T, W>(bMx, xlo, xhi, mxm, x, bm);   // rows past the line end are zero
             band_row<T, W>(bKx, xlo, xhi, mxk, x, bk);
@@ -802,9 +804,11 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
                                      : (a.srcfield ? a.srcfield + (long long)z * plane + (long long)y * sx : sfx);
             const T *fb = LX.fac + b0 * W;
             // kinds: interior segments take bands from registers; the first reads its
-            // head rows (< kHeadRows >= Toeplitz lo) from the table; the last reads
-            // every row from the table (its rows past hi are not Toeplitz)
+            // head rows (< kHeadRows >= Toeplitz lo) from the table, the last its
+            // tail rows (the last kTailRows of the padded line, when they hold
+            // every row from Toeplitz hi on, padding included), else every row
             const bool regular = LX.S >= 2 && xlo <= kHeadRows && xhi >= (LX.S - 1) * SEG && mx >= (LX.S - 1) * SEG + P;
+            const bool tail = xhi >= LX.S * SEG - kTailRows;
             if constexpr (EL) {
                 T x1m[W], x2m[W], x3m[W];
                 const int mid = xlo < xhi ? xlo : 0;
@@ -832,8 +836,10 @@ __device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const RhsElas<T> *
                 phase2_fwd<T, P, SEG, kSegMiddle>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
             else if (regular && s == 0)
                 phase2_fwd<T, P, SEG, kSegFirst>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
-            else if (regular)
+            else if (regular && tail)
                 phase2_fwd<T, P, SEG, kSegLast>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
+            else if (regular)
+                phase2_fwd<T, P, SEG, kSegLastAll>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
             else
                 phase2_fwd<T, P, SEG, kSegGeneral>(row1, row2, mx, b0, mxm, mxk, bMx, bKx, xlo, xhi, fb, srcF, rowF, c2, v);
         }
