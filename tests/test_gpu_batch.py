@@ -192,6 +192,49 @@ def test_profile_rhs_keeps_state():
         s.profile_rhs(0)
 
 
+def test_batch_members_sharing_one_stream():
+    """Members of four degrees and an elasticity simulation on one shared
+    stream: every degree group joins that stream before any group's
+    completion is queued on it, so the groups and the elasticity step run
+    side by side. Each result equals the simulation alone; the state is read
+    back on the shared stream (ads_get_state), so it also checks that the
+    stream waits for every group."""
+    import torch
+    from paper_1911_08158_gb300 import Simulation, batch_step
+    cases = [_mixed_cases()[i] for i in (0, 1, 4, 5)]   # p = 2, 3, 1, 4
+    el = wl.elastic_case(ne=(9, 8, 7), p=2, tau=5e-3, steps=0, seed=4, sigma=0.1)
+    steps = 21
+
+    def make_el(**kw):
+        e = Simulation(el.n_elem, el.p, el.tau, kind="elastic", lam=el.lam, mu=el.mu, rho=el.rho,
+                       precision="fp32", **kw)
+        e.set_gaussian_state(None, el.v0)
+        return e
+
+    alone = []
+    for c in cases:
+        s = _make(c, "fp32")
+        s.step(steps)
+        alone.append(s.get_state())
+        s.close()
+    e = make_el()
+    e.step(steps)
+    el_alone = e.get_state()
+    e.close()
+
+    st = torch.cuda.Stream()
+    sims = [_make(c, "fp32", stream=st) for c in cases]
+    e = make_el(stream=st)
+    batch_step(sims + [e], steps)
+    for s, ref in zip(sims, alone):
+        got = s.get_state()
+        for k in range(3):
+            assert np.array_equal(got[k], ref[k])
+    got = e.get_state()
+    for k in range(2):
+        assert np.array_equal(got[k], el_alone[k])
+
+
 def test_batch_rejects_bad_arguments():
     from paper_1911_08158_gb300 import AdsError, batch_step
     s = _make(wl.pulse_case(ne=6, p=2, steps=0), "fp32")
