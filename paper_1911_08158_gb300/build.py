@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libads_gb300.so")
 SOURCES = ["rhs_f32.cu", "rhs_f32_s33.cu", "rhs_f32_s44.cu", "rhs_f64.cu", "rhs_f64_s33.cu", "rhs_f64_s44.cu",
            "col_f32.cu", "col_f64.cu", "kernels.cu", "api.cpp", "setup1d.cpp",
-           "noalloc.cu", "peaks.cu", "rhs_el_f32.cu", "rhs_el_f64.cu"]
+           "noalloc.cu", "peaks.cu", "rhs_el_f32.cu", "rhs_el_f32_s33.cu", "rhs_el_f32_s44.cu", "rhs_el_f64.cu",
+           "rhs_el_f64_s33.cu", "rhs_el_f64_s44.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -782,9 +782,21 @@ cudaError_t launch_el_to_uv(const T *U, const T *Up, double *u, double *v, long 
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_rhs_el(int p, const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
+{
+    switch (a.lx.seg) {
+    case kSeg: return launch_rhs_el_seg<T, kSeg>(p, a, el, s);
+    case kSegAlt: return launch_rhs_el_seg<T, kSegAlt>(p, a, el, s);
+    case kSegLong: return launch_rhs_el_seg<T, kSegLong>(p, a, el, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 #define ADS_INST(T)                                                                                                \
     template cudaError_t launch_rhs<T>(int, int, const RhsArgs<T> &, cudaStream_t);                                \
     template cudaError_t launch_rhs_group<T>(int, const RhsArgs<T> *, int, cudaStream_t);                         \
+    template cudaError_t launch_rhs_el<T>(int, const RhsArgs<T> &, const RhsElas<T> &, cudaStream_t);             \
     template cudaError_t launch_col<T>(int, int, const ColArgs<T> &, cudaStream_t);                                \
     template cudaError_t launch_axis_apply<T>(int, const T *, int, const T *, T *, Dims, T, T, int, cudaStream_t); \
     template cudaError_t launch_solve_x<T>(int, const T *, T *, Dims, cudaStream_t);                               \

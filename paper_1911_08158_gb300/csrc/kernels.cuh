@@ -206,6 +206,9 @@ cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, in
 // factorisation plus el's extra terms, then the x [and y] sweeps
 template <typename T>
 cudaError_t launch_rhs_el(int p, const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s);
+// the same for segment length SEG (one translation unit each)
+template <typename T, int SEG>
+cudaError_t launch_rhs_el_seg(int p, const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s);
 
 // Sum of Kronecker products in one pass:
 //   out = beta*out + sum_t alpha_t (Ax_t (x) Ay_t (x) Az_t) in_t

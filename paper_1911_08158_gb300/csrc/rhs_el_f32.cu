@@ -1,10 +1,6 @@
-// rhs_el_f32.cu -- instantiation of the elastic K1 launches (float, every segment length).
+// rhs_el_f32.cu -- instantiation of the elastic K1 launches (float, 32-row segments).
 #include "sweep.cuh"
 
 namespace ads {
-template <>
-cudaError_t launch_rhs_el<float>(int p, const RhsArgs<float> &a, const RhsElas<float> &el, cudaStream_t s)
-{
-    return launch_rhs_el_impl<float>(p, a, el, s);
+template cudaError_t launch_rhs_el_seg<float, kSeg>(int, const RhsArgs<float> &, const RhsElas<float> &, cudaStream_t);
 }
-}  // namespace ads

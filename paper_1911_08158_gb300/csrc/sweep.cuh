@@ -1423,22 +1423,14 @@ cudaError_t launch_col_group(int p, const ColArgs<T> *a, const ColMaps *maps, in
 #undef C
 }
 
-// the elastic K1 for every segment length (one translation unit per precision)
-template <typename T>
-cudaError_t launch_rhs_el_impl(int p, const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
+// the elastic K1 of segment length SEG (one translation unit per precision and length)
+template <typename T, int SEG>
+cudaError_t launch_rhs_el_seg(int p, const RhsArgs<T> &a, const RhsElas<T> &el, cudaStream_t s)
 {
-    const int seg = a.lx.seg;
-    if (a.ly.seg != seg) return cudaErrorInvalidValue;
-#define C32(P) rhs_el_layout<T, P, kSeg>(a, el, s)
-#define C33(P) rhs_el_layout<T, P, kSegAlt>(a, el, s)
-#define C44(P) rhs_el_layout<T, P, kSegLong>(a, el, s)
-    if (seg == kSeg) { ADS_DISPATCH_P(p, C32) }
-    if (seg == kSegAlt) { ADS_DISPATCH_P(p, C33) }
-    if (seg == kSegLong) { ADS_DISPATCH_P(p, C44) }
-#undef C32
-#undef C33
-#undef C44
-    return cudaErrorInvalidValue;
+    if (a.lx.seg != SEG || a.ly.seg != SEG) return cudaErrorInvalidValue;
+#define C(P) rhs_el_layout<T, P, SEG>(a, el, s)
+    ADS_DISPATCH_P(p, C)
+#undef C
 }
 
 }  // namespace ads
