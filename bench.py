@@ -75,6 +75,16 @@ def step_flops(p: int) -> dict:
             "step": rhs + 3 * sweep + upd}
 
 
+def hbm_peak():
+    """The measured HBM copy bandwidth of this machine's GPUs (GB/s) and its
+    source, or the fallback figure."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
 def measure_peaks(ads, local):
     """FMA throughput of the device's CUDA cores (ads_measure_fma_peak), with
     the clocks sampled while it runs."""
@@ -504,6 +514,16 @@ def run_elastic(args, stream, flush):
         t = e0.elapsed_time(e1) / 1e3
         dofs = int(np.prod(sim.n)) * 3
         out[prec] = {"value": dofs * case.steps / t, "unit": UNIT, "ms_per_step": t / case.steps * 1e3}
+        if prec == "fp32":
+            # the state alone: U^n and U^{n-1} read, U^{n+1} written once per
+            # interior unknown and step (3 x 4 bytes); the fused schedule moves
+            # more (13 launches a step)
+            peak, src = hbm_peak()
+            interior = int(np.prod([m - 2 for m in sim.n])) * 3
+            ach = interior * case.steps / t * 12 / 1e9
+            out["roofline"] = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src,
+                               "state_bytes_per_interior_dof_step": 12, "achieved_state": round(ach, 1),
+                               "frac_state": round(ach / peak, 4)}
         finals[prec] = sim.get_state(fields=("u",))[0]
         if prec == "fp32":
             out["phases_ms"] = {k: round(v, 4) for k, v in sim.profile_step()}
