@@ -215,13 +215,17 @@ int ads_step(ads_sim_t *sim, int nsteps);
 /* Advance `count` distinct simulations (same device) by nsteps each.
  * Scalar-wave simulations of equal precision and degree, whatever their
  * grids, tiles and sources, advance together: each time step is one grouped
- * launch of K1 over all their z-planes (up to 32 simulations per launch),
- * one of the y sweep for those whose K1 tile does not span y, and one of the
- * z sweep + update; runs of 16 steps replay a captured CUDA graph (cached
+ * launch of K1 over all their z-planes per segment length and CTA layout
+ * present among them (up to 32 simulations per launch), one of the y sweep
+ * for those whose K1 tile does not span y, and one of the z sweep + update
+ * per segment length; runs of 16 steps replay a captured CUDA graph (cached
  * per member set).  Each (precision, degree) group runs on a stream of its
- * own, ordered after the members' streams and before their later work, so
- * groups overlap on the device.  Elasticity simulations step on their own
- * streams.  Every result equals what ads_step gives the simulation alone
+ * own: every group starts after the work already queued on its members'
+ * streams, and those streams wait for their groups before any later work.
+ * All groups join before any completion is queued, and elasticity
+ * simulations step on their own streams after the joins, so groups and
+ * elasticity overlap on the device even when every member shares one
+ * stream.  Every result equals what ads_step gives the simulation alone
  * (the members share no data).  Errors: INVALID_ARG (null or repeated
  * simulation, mixed devices, nsteps < 0), CUDA. */
 int ads_batch_step(ads_sim_t *const *sims, int count, int nsteps);
