@@ -439,9 +439,12 @@ __device__ __forceinline__ void phase1_extra(const T *colx, const long long (&zo
 // Phase 2 of K1, pass 1 for one row segment [b0, b0+n): form
 //   R = F - c2 (Kx s1 + Mx s2)
 // from the s1, s2 rows with a static register window and run the local
-// forward substitution on it.  FAST: a full segment inside the Toeplitz
-// range (no predicates, band rows in registers).
-// Segment kinds of the x-direction pass 1.
+// forward substitution on it.  MODE, the segment kind: kSegMiddle, every row
+// inside the Toeplitz range (band rows in registers, no predicates);
+// kSegFirst, the first segment (its kHeadRows head rows read from the band
+// table); kSegLast / kSegLastAll, the last segment (its kTailRows tail rows,
+// or every row, from the table); kSegGeneral, any segment (each row checks
+// the Toeplitz range).
 enum { kSegMiddle = 0, kSegFirst = 1, kSegLast = 2, kSegGeneral = 3, kSegLastAll = 4 };
 constexpr int kHeadRows = 8;   // leading rows of the first segment read from the band table (>= Toeplitz lo)
 constexpr int kTailRows = 8;   // trailing rows of the last segment read from the table (>= its rows from Toeplitz hi)
