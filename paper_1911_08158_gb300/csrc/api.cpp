@@ -1325,18 +1325,21 @@ int batch_groups(std::map<std::pair<int, int>, std::vector<ads_sim *>> &groups, 
         if (left > 0 && (rc = group_steps(g, r.st, left, true))) return rc;
         for (ads_sim *s : g) s->h_step += nsteps;
     }
-    // 3. the other simulations, queued on their own streams after the joins
-    // above, so they run beside the groups (ads_step takes no batch lock)
+    // 3. each group's completion, recorded before the lock is released (a
+    // group stream is shared by every caller of the same precision and degree)
+    std::vector<cudaEvent_t> done(runs.size());
+    for (size_t i = 0; i < runs.size(); ++i) {
+        if ((rc = new_event(&done[i]))) return rc;
+        ADS_CK(cudaEventRecord(done[i], runs[i].st));
+    }
     lock.unlock();
+    // 4. the other simulations, queued on their own streams after the joins
+    // above, so they run beside the groups (ads_step takes no batch lock)
     for (ads_sim *s : others)
         if ((rc = ads_step(s, nsteps))) return rc;
-    // 4. the members' streams wait for their groups
-    for (Run &r : runs) {
-        cudaEvent_t done;
-        if ((rc = new_event(&done))) return rc;
-        ADS_CK(cudaEventRecord(done, r.st));
-        for (cudaStream_t ms : r.member_streams) ADS_CK(cudaStreamWaitEvent(ms, done, 0));
-    }
+    // 5. the members' streams wait for their groups
+    for (size_t i = 0; i < runs.size(); ++i)
+        for (cudaStream_t ms : runs[i].member_streams) ADS_CK(cudaStreamWaitEvent(ms, done[i], 0));
     return ADS_OK;
 }
 
